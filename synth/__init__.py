@@ -1,0 +1,203 @@
+"""Seeded synthetic inputs shared by the tests, the smoke check and the benchmark.
+
+This module holds no part of the projector arithmetic: it only describes workloads
+(grid, detector and orbit sizes) and draws seeded phantoms, angle lists and noise.
+Both the oracle and the CUDA path consume what it produces.
+
+Workloads (the paper's datasets are not used; every input is synthetic):
+
+* ``fan2d_64``    2D fan beam, 64x64 unit pixels, 90 views over [0, 2pi), 96 elements of
+                  width 1, source-isocentre 200, source-detector 400.
+* ``fan2d_512``   2D fan beam, 512x512, 720 views, 768 elements of width 1,
+                  source-isocentre 1000, source-detector 1500 (batch of 16 phantoms).
+* ``cone3d_128``  3D circular cone beam, 128^3 unit voxels, 180 views, 192x192 detector of
+                  unit pixels, source-isocentre 400, source-detector 800.
+* ``cone3d_512``  3D cone beam, 512^3, 360 views, 768x768 detector, source-isocentre 1000,
+                  source-detector 1500.
+
+Views are phi_v = 2 pi v / N_p, v = 0..N_p-1 (the paper's "equidistant in [0, 2pi)").
+Phantoms are sums of random ellipses (ellipsoids) evaluated at pixel (voxel) centres.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+__all__ = [
+    "CONFIGS", "geometry", "uniform_angles", "ellipse_phantom", "ellipsoid_phantom",
+    "poisson_sinogram", "serving_requests",
+]
+
+
+def uniform_angles(n_views: int) -> np.ndarray:
+    """phi_v = 2 pi v / n_views, v = 0..n_views-1 (float64)."""
+    return 2.0 * math.pi * np.arange(n_views, dtype=np.float64) / n_views
+
+
+def geometry(nx, ny, nz, *, a=1.0, b=1.0, c=1.0, n_views, s, sdd, nu, nv=1, du=1.0,
+             dv=1.0, u_off=0.0, v_off=0.0, angles=None) -> dict:
+    """A workload geometry as a plain dict (lengths in the same unit as the voxel sides)."""
+    if angles is None:
+        angles = uniform_angles(n_views)
+    angles = np.ascontiguousarray(np.asarray(angles, dtype=np.float64))
+    assert angles.shape == (n_views,)
+    return dict(nx=int(nx), ny=int(ny), nz=int(nz), a=float(a), b=float(b), c=float(c),
+                n_views=int(n_views), angles=angles, s=float(s), sdd=float(sdd),
+                nu=int(nu), nv=int(nv), du=float(du), dv=float(dv),
+                u_off=float(u_off), v_off=float(v_off), dim=3 if nz > 1 or nv > 1 else 2)
+
+
+def _fan2d_64():
+    return geometry(64, 64, 1, n_views=90, s=200.0, sdd=400.0, nu=96)
+
+
+def _fan2d_512():
+    return geometry(512, 512, 1, n_views=720, s=1000.0, sdd=1500.0, nu=768)
+
+
+def _cone3d_128():
+    g = geometry(128, 128, 128, n_views=180, s=400.0, sdd=800.0, nu=192, nv=192)
+    g["dim"] = 3
+    return g
+
+
+def _cone3d_512():
+    g = geometry(512, 512, 512, n_views=360, s=1000.0, sdd=1500.0, nu=768, nv=768)
+    g["dim"] = 3
+    return g
+
+
+CONFIGS = {
+    "fan2d_64": _fan2d_64,
+    "fan2d_512": _fan2d_512,
+    "cone3d_128": _cone3d_128,
+    "cone3d_512": _cone3d_512,
+}
+
+
+def config(name: str) -> dict:
+    return CONFIGS[name]()
+
+
+def ellipse_phantom(n: int, seed: int, n_ellipses: int = 10, ny: int | None = None) -> np.ndarray:
+    """Sum of ``n_ellipses`` random ellipses on an n x ny grid of unit pixels centred at 0.
+
+    Centre uniform in the disc of radius 0.7 * n/2; semi-axes U[0.05, 0.35] * n/2;
+    orientation U[0, pi); value U[0, 1].  A pixel takes the sum of the values of the
+    ellipses that contain its centre.  Returns float64 [ny][n].
+    """
+    ny = n if ny is None else ny
+    rng = np.random.default_rng(seed)
+    xs = (np.arange(n) - n / 2.0 + 0.5)
+    ys = (np.arange(ny) - ny / 2.0 + 0.5)
+    X, Y = np.meshgrid(xs, ys)
+    R = 0.5 * min(n, ny)
+    img = np.zeros((ny, n), dtype=np.float64)
+    for _ in range(n_ellipses):
+        r = 0.7 * R * math.sqrt(rng.uniform())
+        th = rng.uniform(0, 2 * math.pi)
+        cx, cy = r * math.cos(th), r * math.sin(th)
+        ax, ay = rng.uniform(0.05, 0.35, size=2) * R
+        ang = rng.uniform(0, math.pi)
+        val = rng.uniform(0, 1)
+        ca, sa = math.cos(ang), math.sin(ang)
+        dx, dy = X - cx, Y - cy
+        xr = dx * ca + dy * sa
+        yr = -dx * sa + dy * ca
+        img[(xr / ax) ** 2 + (yr / ay) ** 2 <= 1.0] += val
+    return img
+
+
+def _random_rotation(rng) -> np.ndarray:
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    w, x, y, z = q
+    return np.array([
+        [1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)],
+        [2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)],
+        [2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)],
+    ])
+
+
+def ellipsoid_phantom(n: int, seed: int, n_ellipsoids: int = 10, dtype=np.float64,
+                      slab: int = 32) -> np.ndarray:
+    """Sum of random ellipsoids on an n^3 grid of unit voxels centred at 0 ([nz][ny][nx]).
+
+    Centre uniform in the ball of radius 0.7 * n/2, semi-axes U[0.05, 0.35] * n/2, a
+    uniformly random rotation, value U[0, 1].  Evaluated slab by slab to bound memory.
+    """
+    rng = np.random.default_rng(seed)
+    R = 0.5 * n
+    params = []
+    for _ in range(n_ellipsoids):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        c = d * 0.7 * R * rng.uniform() ** (1.0 / 3.0)
+        ax = rng.uniform(0.05, 0.35, size=3) * R
+        Rm = _random_rotation(rng)
+        val = rng.uniform(0, 1)
+        params.append((c, ax, Rm, val))
+    out = np.zeros((n, n, n), dtype=dtype)
+    xs = (np.arange(n) - n / 2.0 + 0.5)
+    Y, X = np.meshgrid(xs, xs, indexing="ij")
+    for z0 in range(0, n, slab):
+        zs = xs[z0:z0 + slab]
+        Z = zs[:, None, None]
+        acc = np.zeros((len(zs), n, n), dtype=np.float64)
+        for c, ax, Rm, val in params:
+            dx, dy, dz = X[None] - c[0], Y[None] - c[1], Z - c[2]
+            q = 0.0
+            for r in range(3):
+                comp = Rm[0, r] * dx + Rm[1, r] * dy + Rm[2, r] * dz
+                q = q + (comp / ax[r]) ** 2
+            acc[q <= 1.0] += val
+        out[z0:z0 + slab] = acc
+    return out
+
+
+def poisson_sinogram(p: np.ndarray, seed: int, photons: float = 1e5, max_line: float = 3.0):
+    """Poisson noise at ``photons`` incident counts.
+
+    The clean line integrals are scaled by kappa so that max(kappa p) = ``max_line``;
+    counts ~ Poisson(photons * exp(-kappa p)); the noisy data are
+    -ln(max(count, 1) / photons) / kappa.  Returns (noisy p, kappa).
+    """
+    rng = np.random.default_rng(seed)
+    pmax = float(np.max(p))
+    kappa = max_line / pmax if pmax > 0 else 1.0
+    counts = rng.poisson(photons * np.exp(-kappa * p))
+    noisy = -np.log(np.maximum(counts, 1) / photons) / kappa
+    return noisy.astype(p.dtype), kappa
+
+
+def serving_requests(n_requests: int, seed: int, rate_per_s: float):
+    """Poisson arrivals of reconstruction requests for the serving mix.
+
+    60% 2D (grid N in U{256..1024}, views in U{360..1440}, nu = 1.5 N) and 40% 3D
+    (N in U{64..256}, views in U{90..360}, detector 1.5N x 1.5N).  Geometry follows the
+    512-grid ratios: s = 1.953 N, source-detector = 2.930 N, unit voxels and elements.
+    Each request carries a phantom seed.  Returns a list of dicts with arrival times.
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n_requests):
+        t += rng.exponential(1.0 / rate_per_s)
+        if rng.uniform() < 0.6:
+            n = int(rng.integers(256, 1025))
+            n -= n % 2
+            nviews = int(rng.integers(360, 1441))
+            nu = int(round(1.5 * n))
+            nu += nu % 2
+            g = geometry(n, n, 1, n_views=nviews, s=1.953 * n, sdd=2.930 * n, nu=nu)
+        else:
+            n = int(rng.integers(64, 257))
+            n -= n % 2
+            nviews = int(rng.integers(90, 361))
+            nd = int(round(1.5 * n))
+            nd += nd % 2
+            g = geometry(n, n, n, n_views=nviews, s=1.953 * n, sdd=2.930 * n, nu=nd, nv=nd)
+            g["dim"] = 3
+        out.append(dict(id=i, arrival=t, geom=g, seed=int(rng.integers(0, 2**31 - 1))))
+    return out
