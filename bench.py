@@ -1,0 +1,327 @@
+#!/usr/bin/env python3
+"""Benchmark: fan-beam forward + back projection with the consistent system matrix.
+
+Workload (one step): 2D fan beam, 512x512 unit pixels, 720 views over 360 deg, 768
+detector elements of width 1, source-isocentre 1000, source-detector 1500; a batch of 16
+seeded random-ellipse phantoms in FP32; one step = p = W x over all views, then
+x' = W^T p.  Metric: G voxel-ray updates per second, an update being one nonzero W_ij
+applied to one batch item, counted 2 nnz(W) B per step (forward + back).
+
+Runs one rank per GPU (torchrun for N > 1); every rank projects its own 16 phantoms
+(independent problems: weak scaling, no data-path collective).  ``--impl reference``
+times the FP64 CPU oracle instead (rank 0 only), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+back projector Gvoxel-ray updates/s vs FP64 oracle; served recon p50/p99"
+UNIT = "Gupdates/s"
+WORKLOAD = "fan2d_512"
+BATCH = 16
+# algorithmic FP32 operations per nonzero entry: the weight (two cell atoms and their
+# difference, 12 flops) plus one multiply-add per batch item
+FLOPS_PER_ENTRY_WEIGHT = 12
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------------------
+def cpu_oracle_leg(steps: int, target_s: float = 15.0):
+    """Time the FP64 oracle (as it stands) on the host cores on a sample of the workload:
+    forward + back of one phantom over a subset of views.  Returns a dict."""
+    import numpy as np
+    import oracle
+    import synth
+    g = synth.config(WORKLOAD)
+    x = synth.ellipse_phantom(512, 0)
+    # calibrate the number of views so that one step takes about target_s / steps
+    per_step = max(1.0, target_s / max(steps, 1))
+    v_try = [0, 180, 360, 540]
+    p = oracle.forward_2d(g, x, views=v_try[:1])   # thread-pool start-up, not timed
+    t0 = time.perf_counter()
+    p = oracle.forward_2d(g, x, views=v_try)
+    oracle.back_2d(g, p, views=v_try)
+    t_view = (time.perf_counter() - t0) / len(v_try)
+    n_views = int(max(2, min(720, per_step / max(t_view, 1e-6))))
+    views = (np.arange(n_views) * (720 // n_views if n_views <= 720 else 1)) % 720
+    return g, x, views, oracle.num_threads()
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    g, x, views, cores = cpu_oracle_leg(args.steps)
+    # updates in the sample: the nonzero entries of those views, counted by the oracle
+    nnz_sample = oracle.count_2d(g, views=views)
+    for _ in range(args.warmup):
+        p = oracle.forward_2d(g, x, views=views)
+        oracle.back_2d(g, p, views=views)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        p = oracle.forward_2d(g, x, views=views)
+        oracle.back_2d(g, p, views=views)
+    dt = time.perf_counter() - t0
+    value = 2.0 * nnz_sample * args.steps / dt / 1e9
+    sample = "oracle FP64 fwd+back of 1 phantom over %d of 720 views (%d nonzero entries)" % (len(views), nnz_sample)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (sampled views)", "batch": 1,
+                                        "views": int(len(views))},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    try:
+        import paper_2511_12235_gb300 as csm
+    except ImportError:
+        from paper_2511_12235_gb300 import build
+        build.build()
+        import paper_2511_12235_gb300 as csm
+    import synth
+
+    g = synth.config(WORKLOAD)
+    seeds = range(rank * BATCH, (rank + 1) * BATCH)
+    xs_host = np.stack([synth.ellipse_phantom(512, s) for s in seeds]).astype(np.float32)
+    x = torch.from_numpy(xs_host).to(dev)
+    P = csm.Projector(g, device=dev)
+    nnz = P.nnz()
+    stream = torch.cuda.current_stream(dev)
+    p = torch.empty((BATCH,) + P.sino_shape, dtype=torch.float32, device=dev)
+    xb = torch.empty((BATCH,) + P.vol_shape, dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        P.forward(x, out=p)
+        P.back(p, out=xb)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    # --- timed region: K steps, L2 flushed before each (flush not timed) ---------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    clocks.start()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        evs[i][0].record(stream)
+        step()
+        evs[i][1].record(stream)
+    barrier()
+    clk = clocks.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+
+    # --- per-kernel timing for the roofline: forward alone, back alone ------------------
+    def time_op(fn, n=5):
+        es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for i in range(n):
+            flush.fill_(float(i))
+            es[i][0].record(stream)
+            fn()
+            es[i][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in es) / n
+
+    t_fwd = time_op(lambda: P.forward(x, out=p))
+    t_back = time_op(lambda: P.back(p, out=xb))
+
+    # --- end to end through the public API with host buffers ----------------------------
+    x_pin = torch.from_numpy(xs_host).pin_memory()
+    out_pin = torch.empty((BATCH,) + P.vol_shape, dtype=torch.float32).pin_memory()
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ee[i][0].record(stream)
+        xd = x_pin.to(dev, non_blocking=True)
+        pp = P.forward(xd)
+        r = P.back(pp)
+        out_pin.copy_(r, non_blocking=True)
+        ee[i][1].record(stream)
+    barrier()
+    t_e2e = sum(a.elapsed_time(b) for a, b in ee)
+
+    # max over ranks
+    tt = torch.tensor([t_ms, t_e2e, t_fwd, t_back], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    t_ms, t_e2e, t_fwd, t_back = tt.tolist()
+
+    updates_per_step = 2.0 * nnz * BATCH * world
+    value = updates_per_step * args.steps / (t_ms / 1e3) / 1e9
+    e2e_value = updates_per_step * args.steps / (t_e2e / 1e3) / 1e9
+
+    # roofline of the dominant kernel (ALU bound: algorithmic flops / launch time)
+    dom, t_dom = ("forward", t_fwd) if t_fwd >= t_back else ("back", t_back)
+    flops = nnz * (FLOPS_PER_ENTRY_WEIGHT + 2 * BATCH)
+    achieved = flops / (t_dom / 1e3) / 1e12
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_alu_peak_tflops(sm_max)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [512, 512], "views": 720, "detector": 768, "batch": BATCH,
+                   "nnz_per_phantom": nnz, "l2": "flushed before every timed step (512 MiB write, untimed)",
+                   "step": "forward over all views + back projection, batch of 16"},
+        "gpu_launches": 4 * args.steps,
+        "kernels_ms": {"forward": t_fwd, "back": t_back},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x %.0f MHz (max SM clock); "
+                                  "algorithmic flops = nnz x (%d + 2 x batch)" % (sm_max, FLOPS_PER_ENTRY_WEIGHT)},
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_pin.numel() * 4),
+                "d2h_bytes_per_step": int(out_pin.numel() * 4)},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            import oracle
+            gq, xq, views, cores = cpu_oracle_leg(1, target_s=12.0)
+            n_sample = oracle.count_2d(gq, views=views)
+            t0 = time.perf_counter()
+            pq = oracle.forward_2d(gq, xq, views=views)
+            oracle.back_2d(gq, pq, views=views)
+            dt = time.perf_counter() - t0
+            line["cpu_baseline"] = {
+                "value": 2.0 * n_sample / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "FP64 oracle fwd+back of 1 phantom over %d of 720 views (%d entries), %.1f s"
+                          % (len(views), n_sample, dt)}
+        except Exception as e:  # the baseline is reported, not required
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
+                                    "sample": "failed: %s" % e}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    P.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

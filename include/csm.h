@@ -1,0 +1,139 @@
+/*
+ * csm.h -- C ABI of the consistent cone-beam system-matrix projectors (sm_103a).
+ *
+ * The library applies the system matrix W of "Computation of a Consistent System Matrix
+ * for Cone-beam Computed Tomography" without storing it: every entry W_ij is the exact
+ * area (2D fan beam) or volume (3D circular cone beam) of the intersection of voxel j with
+ * the cone from the source to detector element i (Introduction, Eq. (ip): p = W u), and is
+ * evaluated on the fly from closed-form triangle / trapezoid atoms (2D, Sections
+ * "Triangle", "Trapezoid", Eq. (2d procedure)) and from their 3D extension (Section "The
+ * Three-dimensional Case", Eq. (rel vol 3d), Eq. (res vol 3d)).
+ *
+ * Geometry (Section "Notation and Setup", Eq. (z rotation)): the source sits at
+ * (s cos phi, s sin phi, 0) and rotates about z; the flat detector lies at distance
+ * sdd - s behind the isocentre, perpendicular to the source-isocentre ray.  A point P is
+ * seen at detector coordinates u = sdd (-P_x sin phi + P_y cos phi) / t and
+ * v = sdd P_z / t with depth t = s - P_x cos phi - P_y sin phi.  Detector corner k lies at
+ * u_k = (k - nu/2) du + u_off (rows: v_l = (l - nv/2) dv + v_off); element k spans
+ * [u_k, u_{k+1}].  The voxel grid is centred on the origin: voxel i spans
+ * [(i - nx/2) a, (i + 1 - nx/2) a] (likewise y with b, z with c).
+ *
+ * Memory layouts (all contiguous, batch outermost, caller-owned device memory):
+ *   volume    x[batch][nz][ny][nx]        (2D: nz = 1)
+ *   sinogram  p[batch][n_views][nv][nu]   (2D: nv = 1)
+ *
+ * Every call is asynchronous on the given CUDA stream (NULL = legacy default stream).
+ * Argument errors are returned synchronously; a failed kernel launch returns
+ * CSM_ECUDA.  Nothing aborts the process.  The library owns only the device geometry
+ * table created by csm_geom_create_*; every other buffer (inputs, outputs, workspace)
+ * belongs to the caller.
+ */
+#ifndef CSM_H_
+#define CSM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct csm_geom_s* csm_geom_t;
+
+typedef enum {
+    CSM_OK = 0,
+    CSM_EINVAL = 1,         /* bad argument (NULL pointer, size, dtype, workspace too small) */
+    CSM_EGEOM = 2,          /* geometry not supported (e.g. source inside the grid's circle) */
+    CSM_ENOMEM = 3,         /* the geometry table could not be allocated                    */
+    CSM_ECUDA = 4,          /* a CUDA call failed; see csm_last_cuda_error()                 */
+    CSM_EUNSUPPORTED = 5,   /* valid request that this build does not implement              */
+    CSM_ETIMEOUT = 6        /* a bounded device-side wait gave up                            */
+} csm_status;
+
+typedef enum { CSM_F32 = 0, CSM_F64 = 1, CSM_BF16 = 2, CSM_F16 = 3 } csm_dtype;
+
+/* flags for csm_forward / csm_back */
+#define CSM_ACCUMULATE        1   /* add into the output instead of overwriting it           */
+#define CSM_RELATIVE_WEIGHTS  2   /* entries divided by the voxel measure ab (abc), as in the
+                                     paper's A_3, A_4, Vol_rel                                */
+#define CSM_VOXEL_DRIVEN      4   /* forward only: voxel-driven scatter variant (else the
+                                     ray-driven gather variant)                               */
+
+/* 2D fan-beam geometry.  angles == NULL means phi_v = 2 pi v / n_views. */
+typedef struct {
+    int nx, ny;              /* pixel grid                                     */
+    double a, b;             /* pixel sides in x, y                            */
+    int n_views;             /* number of gantry angles                        */
+    const double* angles;    /* host array of n_views angles [rad] or NULL     */
+    double s;                /* source - isocentre distance                    */
+    double sdd;              /* source - detector distance s + d               */
+    int nu;                  /* detector elements                              */
+    double du;               /* element width d_y                              */
+    double u_off;            /* detector shift along u                         */
+} csm_geom2d_desc;
+
+/* 3D circular cone-beam geometry (rotation about z). */
+typedef struct {
+    int nx, ny, nz;
+    double a, b, c;
+    int n_views;
+    const double* angles;
+    double s, sdd;
+    int nu, nv;              /* detector columns (u) and rows (v)              */
+    double du, dv;           /* element sizes d_y, d_z                         */
+    double u_off, v_off;
+} csm_geom3d_desc;
+
+/* Validate a 2D geometry and build its device table (Eq. (beta_computation): the rays to
+ * the detector corners; Appendix Eq. (y expression), Eq. (x expression): each corner ray
+ * as a line across the pixel grid).  Requires s > the grid's circumradius and sdd > s
+ * (the cone lies between source and detector), positive sizes.  Must be called with the
+ * target device current.  On success *out owns device memory until csm_geom_free.
+ * Errors: CSM_EINVAL (NULL / non-positive sizes), CSM_EGEOM, CSM_ENOMEM, CSM_ECUDA. */
+csm_status csm_geom_create_2d(const csm_geom2d_desc* desc, csm_geom_t* out);
+
+/* Same for the 3D geometry (Section "The Three-dimensional Case"). */
+csm_status csm_geom_create_3d(const csm_geom3d_desc* desc, csm_geom_t* out);
+
+/* Release the geometry (synchronises the device with cudaFree).  NULL is ignored. */
+void csm_geom_free(csm_geom_t geom);
+
+/* Bytes of caller-provided device workspace that csm_forward / csm_back need for this
+ * geometry, batch and arithmetic type (op: 0 = forward, 1 = back).  The workspace holds
+ * the batch-interleaved copies of the input that the kernels gather from. */
+csm_status csm_workspace_bytes(csm_geom_t geom, int op, int64_t batch, csm_dtype compute,
+                               size_t* bytes);
+
+/* p = W x  (Algorithm 1, "Computation of W in 2D", and its 3D counterpart).
+ *   x : device pointer, x_dt elements, layout x[batch][nz][ny][nx]
+ *   p : device pointer, p_dt elements, layout p[batch][n_views][nv][nu]
+ *   Arithmetic is FP64 when x_dt or p_dt is CSM_F64, else FP32 (BF16/F16 are storage
+ *   types only).  workspace: device pointer of at least csm_workspace_bytes(op = 0);
+ *   may alias neither x nor p.  Returns CSM_EINVAL when the workspace is too small. */
+csm_status csm_forward(csm_geom_t geom, const void* x, void* p, int64_t batch,
+                       csm_dtype x_dt, csm_dtype p_dt, int flags,
+                       void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* x = W^T p, the adjoint of csm_forward with the same entries (Section "Algorithm 1" and
+ * the paper's adjoint-mismatch check, Section "Numerical Experiments").  Gather form: one
+ * thread per voxel, no atomics.  Arguments as for csm_forward with the roles of x and p
+ * exchanged (workspace from csm_workspace_bytes(op = 1)). */
+csm_status csm_back(csm_geom_t geom, const void* p, void* x, int64_t batch,
+                    csm_dtype p_dt, csm_dtype x_dt, int flags,
+                    void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* Number of nonzero entries of W for this geometry (voxel, view, element with a positive
+ * intersection), computed once on the device and cached.  Synchronises the stream. */
+csm_status csm_nnz(csm_geom_t geom, int64_t* nnz, void* cuda_stream);
+
+/* Waits for the stream and reports an asynchronous kernel failure as CSM_ECUDA. */
+csm_status csm_sync_status(void* cuda_stream);
+
+const char* csm_status_string(csm_status status);
+/* Text of the last CUDA error seen by the library in this thread ("" if none). */
+const char* csm_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSM_H_ */

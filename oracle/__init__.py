@@ -84,6 +84,8 @@ def _load():
         lib.orc2d_coo.restype = C.c_long
         lib.orc3d_coo.argtypes = [gp, ip, C.c_int, ip, ip, dp, C.c_long]
         lib.orc3d_coo.restype = C.c_long
+        lib.orc2d_count.argtypes = [gp, ip, C.c_int]
+        lib.orc2d_count.restype = C.c_long
         lib.orc_num_threads.restype = C.c_int
         _lib = lib
         return lib
@@ -225,6 +227,13 @@ def back_voxel_3d(g: dict, p: np.ndarray, ix: int, iy: int, iz: int, views=None)
     v = _views(g, views)
     p = np.ascontiguousarray(p, dtype=np.float64)
     return float(_load().orc3d_back_voxel(h.ref, _dptr(p), _iptr(v), len(v), int(ix), int(iy), int(iz)))
+
+
+def count_2d(g: dict, views=None) -> int:
+    """Number of nonzero 2D entries over the given views."""
+    h = _GeomHolder(g)
+    v = _views(g, views)
+    return int(_load().orc2d_count(h.ref, _iptr(v), len(v)))
 
 
 def coo(g: dict, views=None, cap: int | None = None):

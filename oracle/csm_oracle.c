@@ -524,6 +524,19 @@ long orc3d_coo(const orc_geom* g, const int* views, int nsel, int* rows, int* co
     return cnt;
 }
 
+/* Number of nonzero 2D entries over the selected views (for rate accounting). */
+long orc2d_count(const orc_geom* g, const int* views, int nsel) {
+    long total = 0;
+    #pragma omp parallel for schedule(dynamic, 1) reduction(+:total)
+    for (int vi = 0; vi < nsel; ++vi) {
+        int ks[64]; double ws[64];
+        for (int iy = 0; iy < g->ny; ++iy)
+            for (int ix = 0; ix < g->nx; ++ix)
+                total += orc2d_entries(g, views[vi], ix, iy, 0, ks, ws, 64);
+    }
+    return total;
+}
+
 long orc2d_coo(const orc_geom* g, const int* views, int nsel, int* rows, int* cols, double* vals, long cap) {
     long cnt = 0;
     int ks[64]; double ws[64];

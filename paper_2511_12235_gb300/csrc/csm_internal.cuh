@@ -1,0 +1,229 @@
+// csm_internal.cuh -- geometry handle, kernel parameter blocks and the shared device math
+// of the projectors.  Included by every translation unit of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/csm.h"
+
+namespace csm {
+
+// ---------------------------------------------------------------------------------------
+// Geometry handle (host).  The device block holds, per view:
+//   axis_sigma[v] = {axis, sigma}: axis 0 walks the grid along x (pixel columns) and writes
+//       every corner ray as a line y(x); axis 1 walks along y with lines x(y).  sigma = +1
+//       when the line of corner k+1 lies above (larger cross coordinate) the line of k.
+//   cs[v]       = {cos phi, sin phi}
+//   line_fx     = per corner k: the line's cross coordinate in cell units at walk boundary
+//                 w = 0 and its step per cell, both 32.32 fixed point (int64)
+//   line_d      = the same two numbers in double
+//   inv2        = 1 / (2 |step|) per corner (float and double)
+//   wrange      = per element k: the walk cells [w0, w1) where its strip meets the grid
+//   rows (3D)   = per row corner l: q_l = v_l / sdd (float and double)
+// ---------------------------------------------------------------------------------------
+struct DeviceTables {
+    int* axis_sigma = nullptr;     // [V][2]
+    float* cs_f = nullptr;         // [V][2]
+    double* cs_d = nullptr;        // [V][2]
+    long long* line_fx = nullptr;  // [V][nu+1][2]
+    double* line_d = nullptr;      // [V][nu+1][2]
+    float* inv_f = nullptr;        // [V][nu+1]
+    double* inv_d = nullptr;       // [V][nu+1]
+    int* wrange = nullptr;         // [V][nu][2]
+    float* rowq_f = nullptr;       // [nv+1]
+    double* rowq_d = nullptr;      // [nv+1]
+    unsigned long long* counter = nullptr;  // scratch word for csm_nnz
+};
+
+}  // namespace csm
+
+struct csm_geom_s {
+    int dim = 2;
+    int nx = 0, ny = 0, nz = 1;
+    double a = 1, b = 1, c = 1;
+    int n_views = 0;
+    std::vector<double> angles;
+    double s = 0, sdd = 0;
+    int nu = 0, nv = 1;
+    double du = 1, dv = 1, u_off = 0, v_off = 0;
+    int device = 0;
+    void* d_block = nullptr;
+    size_t d_bytes = 0;
+    csm::DeviceTables t;
+    int64_t nnz = -1;
+};
+
+namespace csm {
+
+// Parameters passed by value to the kernels.
+struct Geo {
+    int nx, ny, nz, nu, nv, n_views;
+    // grid and detector in float and double
+    float a, b, c, s, sdd, du, dv, u0, v0, x0, y0, z0;
+    double a_d, b_d, c_d, s_d, sdd_d, du_d, dv_d, u0_d, v0_d, x0_d, y0_d, z0_d;
+    const int* axis_sigma;
+    const float* cs_f;
+    const double* cs_d;
+    const long long* line_fx;
+    const double* line_d;
+    const float* inv_f;
+    const double* inv_d;
+    const int* wrange;
+    const float* rowq_f;
+    const double* rowq_d;
+};
+
+Geo make_geo(const csm_geom_s* g);
+
+// thread-local record of the last CUDA error text
+void set_cuda_error(cudaError_t e);
+csm_status check_launch();
+
+// ---------------------------------------------------------------------------------------
+// Element conversions for storage types.
+// ---------------------------------------------------------------------------------------
+template <typename S> __device__ __forceinline__ float to_f(S v);
+template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f<double>(double v) { return (float)v; }
+template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
+
+template <typename T, typename S> __device__ __forceinline__ T load_as(const S* p) { return (T)to_f<S>(*p); }
+template <> __device__ __forceinline__ double load_as<double, double>(const double* p) { return *p; }
+template <> __device__ __forceinline__ float load_as<float, float>(const float* p) { return *p; }
+
+template <typename S> __device__ __forceinline__ S from_f(float v);
+template <> __device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_f<double>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_f<__half>(float v) { return __float2half_rn(v); }
+
+template <typename S, typename T> __device__ __forceinline__ void store_as(S* p, T v, bool acc) {
+    float cur = acc ? to_f<S>(*p) : 0.0f;
+    *p = from_f<S>(cur + (float)v);
+}
+template <> __device__ __forceinline__ void store_as<double, double>(double* p, double v, bool acc) {
+    *p = acc ? *p + v : v;
+}
+template <> __device__ __forceinline__ void store_as<float, float>(float* p, float v, bool acc) {
+    *p = acc ? *p + v : v;
+}
+
+// ---------------------------------------------------------------------------------------
+// The 2D atom: the fraction of a unit cell lying below a straight line.
+//
+// Walking the grid along one axis, every corner ray is a straight line across a cell.  Its
+// cross coordinates at the two walk-faces of the cell, measured in cell units from the
+// cell's lower cross-face, are p and q.  The part of the cell below the line is
+//   - a trapezoid when the line crosses both walk-faces inside the cell (the paper's A_4
+//     between two such rays, Eq. (area trapezoid rel): height x mid-line),
+//   - a corner triangle, or the cell minus one, when the line leaves through a cross-face
+//     (the paper's A_3, Section "Triangle"),
+// i.e. clamp(line, 0, 1) integrated over the cell.  With relu(y) - relu(y - 1) = clamp and
+// the exact mean of relu over a linear segment,
+//      mean_{tau in [0,1]} relu(p + (q - p) tau) = (p + q)/2            if p, q >= 0
+//                                              = 0                       if p, q <= 0
+//                                              = max(p,q)^2 / (2|q - p|) otherwise,
+// where 1 / (2|q - p|) is a per-line constant (the line's step per cell), so the atom needs
+// no division.  An element's weight is the difference of the atoms of its two corner rays
+// (the cumulative form of the sums and differences of Eq. (2d procedure)).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T relu_mean(T p, T q, T inv2) {
+    T mx = p > q ? p : q;
+    T mn = p > q ? q : p;
+    if (mn >= T(0)) return T(0.5) * (p + q);
+    if (mx <= T(0)) return T(0);
+    return mx * mx * inv2;
+}
+
+template <typename T>
+__device__ __forceinline__ T cell_below(T p, T q, T inv2) {
+    T mx = p > q ? p : q;
+    T mn = p > q ? q : p;
+    if (mn >= T(1)) return T(1);
+    if (mx <= T(0)) return T(0);
+    if (mn >= T(0) && mx <= T(1)) return T(0.5) * (p + q);
+    return relu_mean(p, q, inv2) - relu_mean(p - T(1), q - T(1), inv2);
+}
+
+// Cross coordinate of a corner line relative to cell c, at walk boundaries w and w+1.
+// Float path: 32.32 fixed point, exact stepping, so the local offset carries no error from
+// the magnitude of the absolute position.  Double path: double arithmetic.
+struct LineF {
+    long long p, d;   // position at walk boundary w, step per cell
+    __device__ __forceinline__ void load(const Geo& g, int v, int k, int w) {
+        const long long* e = g.line_fx + 2 * ((size_t)v * (g.nu + 1) + k);
+        d = e[1];
+        p = e[0] + (long long)w * d;
+    }
+    __device__ __forceinline__ void step() { p += d; }
+    __device__ __forceinline__ int cell_lo() const {   // floor of min(position at w, w+1)
+        long long q = p + d;
+        return (int)((p < q ? p : q) >> 32);
+    }
+    __device__ __forceinline__ int cell_hi() const {
+        long long q = p + d;
+        return (int)((p > q ? p : q) >> 32);
+    }
+    static __device__ __forceinline__ float local(long long P, int c) {
+        int hi = (int)(P >> 32);
+        unsigned lo = (unsigned)(P & 0xffffffffull);
+        return (float)(hi - c) + (float)lo * 2.3283064365386963e-10f;
+    }
+    __device__ __forceinline__ void offsets(int c, float& ya, float& yb) const {
+        ya = local(p, c);
+        yb = local(p + d, c);
+    }
+};
+
+struct LineD {
+    double p, d;
+    __device__ __forceinline__ void load(const Geo& g, int v, int k, int w) {
+        const double* e = g.line_d + 2 * ((size_t)v * (g.nu + 1) + k);
+        d = e[1];
+        p = e[0] + (double)w * d;
+    }
+    __device__ __forceinline__ void step() { p += d; }
+    __device__ __forceinline__ int cell_lo() const { return (int)floor(fmin(p, p + d)); }
+    __device__ __forceinline__ int cell_hi() const { return (int)floor(fmax(p, p + d)); }
+    __device__ __forceinline__ void offsets(int c, double& ya, double& yb) const {
+        ya = p - (double)c;
+        yb = (p + d) - (double)c;
+    }
+};
+
+template <typename T> struct LineOf;
+template <> struct LineOf<float> { using type = LineF; };
+template <> struct LineOf<double> { using type = LineD; };
+
+template <typename T> __device__ __forceinline__ T inv_of(const Geo& g, int v, int k);
+template <> __device__ __forceinline__ float inv_of<float>(const Geo& g, int v, int k) {
+    return g.inv_f[(size_t)v * (g.nu + 1) + k];
+}
+template <> __device__ __forceinline__ double inv_of<double>(const Geo& g, int v, int k) {
+    return g.inv_d[(size_t)v * (g.nu + 1) + k];
+}
+
+// Launch entry points implemented per dimension.
+csm_status forward_2d(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt,
+                      csm_dtype pdt, int flags, void* ws, size_t ws_bytes, cudaStream_t st);
+csm_status back_2d(const csm_geom_s* g, const void* p, void* x, int64_t batch, csm_dtype pdt,
+                   csm_dtype xdt, int flags, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t workspace_2d(const csm_geom_s* g, int op, int64_t batch, bool dbl);
+csm_status nnz_2d(const csm_geom_s* g, int64_t* out, cudaStream_t st);
+
+csm_status forward_3d(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt,
+                      csm_dtype pdt, int flags, void* ws, size_t ws_bytes, cudaStream_t st);
+csm_status back_3d(const csm_geom_s* g, const void* p, void* x, int64_t batch, csm_dtype pdt,
+                   csm_dtype xdt, int flags, void* ws, size_t ws_bytes, cudaStream_t st);
+size_t workspace_3d(const csm_geom_s* g, int op, int64_t batch, bool dbl);
+csm_status nnz_3d(const csm_geom_s* g, int64_t* out, cudaStream_t st);
+
+}  // namespace csm

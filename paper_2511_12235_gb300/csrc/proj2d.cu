@@ -1,0 +1,403 @@
+// proj2d.cu -- 2D fan-beam projectors: p = W x (ray-driven gather) and x = W^T p
+// (voxel-driven gather), with every entry W_ij evaluated on the fly.
+//
+// Entry of W (Introduction, Eq. (ip)): the area of pixel j inside the fan of element k,
+// i.e. between the rays to detector corners k and k+1.  Each view walks the grid along one
+// axis (the paper's frame rotation by pi/2 so that the rays cross the walked cells from
+// one walk-face to the other, Section "The Two-dimensional Case"); inside a cell every corner
+// ray is a straight line, the area below it is a trapezoid or a corner triangle (the
+// paper's A_4 and A_3 atoms), and the element's area is the difference of the two corner
+// rays' atoms (the sums / differences of Eq. (2d procedure) in cumulative form).
+#include <algorithm>
+
+#include "csm_internal.cuh"
+
+namespace csm {
+
+static int chunk_for(int64_t batch) {
+    if (batch >= 16) return 16;
+    if (batch >= 8) return 8;
+    if (batch >= 4) return 4;
+    if (batch >= 2) return 2;
+    return 1;
+}
+
+static size_t al256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+size_t workspace_2d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
+    if (batch <= 0) return 0;
+    const size_t es = dbl ? 8 : 4;
+    const size_t nb = chunk_for(batch);
+    if (op == 0) return 2 * al256((size_t)g->nx * g->ny * nb * es);
+    return al256((size_t)g->n_views * g->nu * nb * es);
+}
+
+// ---------------------------------------------------------------------------------------
+// Layout kernels: gather a chunk of NB batch items into pixel-major, batch-interleaved
+// copies (one per walk axis) so that the projector reads NB contiguous values per cell.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T load_any(const void* base, size_t i, int dt) {
+    switch (dt) {
+        case CSM_F64: return (T)((const double*)base)[i];
+        case CSM_BF16: return (T)__bfloat162float(((const __nv_bfloat16*)base)[i]);
+        case CSM_F16: return (T)__half2float(((const __half*)base)[i]);
+        default: return (T)((const float*)base)[i];
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_any(void* base, size_t i, int dt, T v, bool acc) {
+    switch (dt) {
+        case CSM_F64: { double* q = (double*)base + i; *q = acc ? *q + (double)v : (double)v; break; }
+        case CSM_BF16: {
+            __nv_bfloat16* q = (__nv_bfloat16*)base + i;
+            float cur = acc ? __bfloat162float(*q) : 0.0f;
+            *q = __float2bfloat16_rn(cur + (float)v);
+            break;
+        }
+        case CSM_F16: {
+            __half* q = (__half*)base + i;
+            float cur = acc ? __half2float(*q) : 0.0f;
+            *q = __float2half_rn(cur + (float)v);
+            break;
+        }
+        default: { float* q = (float*)base + i; *q = acc ? *q + (float)v : (float)v; break; }
+    }
+}
+
+// x[b][iy][ix] -> xs0[(ix*ny + iy)*NB + bb] (walk x) and xs1[(iy*nx + ix)*NB + bb] (walk y)
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) prep_image_2d(const void* __restrict__ x, int xdt, int B, int b_off,
+                                                     int nx, int ny, T* __restrict__ xs0, T* __restrict__ xs1) {
+    __shared__ T tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int bb = 0; bb < NB; ++bb) {
+        const int b = b_off + bb;
+        for (int j = ty; j < 32; j += 8) {
+            int ix = bx + tx, iy = by + j;
+            T val = T(0);
+            if (ix < nx && iy < ny && b < B) val = load_any<T>(x, ((size_t)b * ny + iy) * nx + ix, xdt);
+            tile[j][tx] = val;
+            if (ix < nx && iy < ny) xs1[((size_t)iy * nx + ix) * NB + bb] = val;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            int ix = bx + j, iy = by + tx;
+            if (ix < nx && iy < ny) xs0[((size_t)ix * ny + iy) * NB + bb] = tile[tx][j];
+        }
+        __syncthreads();
+    }
+}
+
+// p[b][v][k] -> ps[(v*nu + k)*NB + bb]
+template <typename T, int NB>
+__global__ void prep_sino_2d(const void* __restrict__ p, int pdt, int B, int b_off, int V, int nu,
+                             T* __restrict__ ps) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)V * nu) return;
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb) {
+        const int b = b_off + bb;
+        ps[i * NB + bb] = b < B ? load_any<T>(p, (size_t)b * V * nu + i, pdt) : T(0);
+    }
+}
+
+template <typename T, int NB>
+__device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict__ xp) {
+    if constexpr (sizeof(T) == 4 && NB % 4 == 0) {
+        const float4* q = reinterpret_cast<const float4*>(xp);
+#pragma unroll
+        for (int i = 0; i < NB / 4; ++i) {
+            float4 v = __ldg(q + i);
+            acc[4 * i + 0] += wt * v.x;
+            acc[4 * i + 1] += wt * v.y;
+            acc[4 * i + 2] += wt * v.z;
+            acc[4 * i + 3] += wt * v.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc[i] += wt * __ldg(xp + i);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Forward, ray-driven: one thread per (view, element).  The thread walks the cells of its
+// fan strip along the view's walk axis; in each walked column it visits the cells between
+// its two corner lines and accumulates  W * x  for NB batch items.
+// ---------------------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(128) fwd2d_ray(Geo g, const T* __restrict__ xs0, const T* __restrict__ xs1,
+                                                 void* __restrict__ p, int pdt, int B, int b_off, T scale,
+                                                 int accumulate) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int v = blockIdx.y;
+    if (k >= g.nu) return;
+    const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+    const int nc = axis == 0 ? g.ny : g.nx;
+    const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
+    const int w0 = g.wrange[2 * ((size_t)v * g.nu + k)], w1 = g.wrange[2 * ((size_t)v * g.nu + k) + 1];
+    using L = typename LineOf<T>::type;
+    L la, lb;
+    la.load(g, v, k, w0);
+    lb.load(g, v, k + 1, w0);
+    const T ia = inv_of<T>(g, v, k), ib = inv_of<T>(g, v, k + 1);
+    T acc[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) acc[i] = T(0);
+    for (int w = w0; w < w1; ++w) {
+        int clo = min(la.cell_lo(), lb.cell_lo());
+        int chi = max(la.cell_hi(), lb.cell_hi());
+        clo = max(clo, 0);
+        chi = min(chi, nc - 1);
+        for (int c = clo; c <= chi; ++c) {
+            T a0, a1, b0, b1;
+            la.offsets(c, a0, a1);
+            lb.offsets(c, b0, b1);
+            const T fa = cell_below(a0, a1, ia), fb = cell_below(b0, b1, ib);
+            const T wt = sigma > 0 ? fb - fa : fa - fb;
+            if (wt != T(0)) fma_cell<T, NB>(acc, wt, xs + ((size_t)w * nc + c) * NB);
+        }
+        la.step();
+        lb.step();
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = b_off + i;
+        if (b < B) store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k, pdt, acc[i] * scale, accumulate != 0);
+    }
+}
+
+template <typename T> __device__ __forceinline__ T cs_of(const Geo& g, int v, int i);
+template <> __device__ __forceinline__ float cs_of<float>(const Geo& g, int v, int i) { return g.cs_f[2 * v + i]; }
+template <> __device__ __forceinline__ double cs_of<double>(const Geo& g, int v, int i) { return g.cs_d[2 * v + i]; }
+
+template <typename T> struct GeoT;
+template <> struct GeoT<float> {
+    static __device__ __forceinline__ float s(const Geo& g) { return g.s; }
+    static __device__ __forceinline__ float sdd(const Geo& g) { return g.sdd; }
+    static __device__ __forceinline__ float u0(const Geo& g) { return g.u0; }
+    static __device__ __forceinline__ float du(const Geo& g) { return g.du; }
+    static __device__ __forceinline__ float x0(const Geo& g) { return g.x0; }
+    static __device__ __forceinline__ float y0(const Geo& g) { return g.y0; }
+    static __device__ __forceinline__ float a(const Geo& g) { return g.a; }
+    static __device__ __forceinline__ float b(const Geo& g) { return g.b; }
+};
+template <> struct GeoT<double> {
+    static __device__ __forceinline__ double s(const Geo& g) { return g.s_d; }
+    static __device__ __forceinline__ double sdd(const Geo& g) { return g.sdd_d; }
+    static __device__ __forceinline__ double u0(const Geo& g) { return g.u0_d; }
+    static __device__ __forceinline__ double du(const Geo& g) { return g.du_d; }
+    static __device__ __forceinline__ double x0(const Geo& g) { return g.x0_d; }
+    static __device__ __forceinline__ double y0(const Geo& g) { return g.y0_d; }
+    static __device__ __forceinline__ double a(const Geo& g) { return g.a_d; }
+    static __device__ __forceinline__ double b(const Geo& g) { return g.b_d; }
+};
+
+// Elements [k0, k1] whose interval can meet the pixel's projection: the detector
+// coordinates of its corners (Appendix Eq. (tan beta): u = sdd tan gamma).  The range is
+// widened by a margin far above the rounding error of u (1e-3 element in FP32), so an
+// element is never missed; an element included by the margin gets an exact zero weight.
+template <typename T> __device__ __forceinline__ T quick_div(T a, T b) { return a / b; }
+template <> __device__ __forceinline__ float quick_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename T> struct RangeEps;
+template <> struct RangeEps<float> { static constexpr float v = 1e-3f; };
+template <> struct RangeEps<double> { static constexpr double v = 1e-9; };
+
+template <typename T>
+__device__ __forceinline__ bool pixel_elements(const Geo& g, int v, T X0, T X1, T Y0, T Y1, int& k0, int& k1) {
+    const T c = cs_of<T>(g, v, 0), sn = cs_of<T>(g, v, 1);
+    const T s = GeoT<T>::s(g), D = GeoT<T>::sdd(g);
+    T umin = T(1e30), umax = T(-1e30);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const T X = (q & 1) ? X1 : X0, Y = (q & 2) ? Y1 : Y0;
+        const T t = s - X * c - Y * sn;
+        const T u = quick_div<T>(D * (Y * c - X * sn), t);
+        umin = u < umin ? u : umin;
+        umax = u > umax ? u : umax;
+    }
+    const T inv_du = T(1) / GeoT<T>::du(g);
+    T f0 = floor((umin - GeoT<T>::u0(g)) * inv_du - RangeEps<T>::v);
+    T f1 = floor((umax - GeoT<T>::u0(g)) * inv_du + RangeEps<T>::v);
+    f0 = f0 < T(-2) ? T(-2) : (f0 > T(g.nu + 2) ? T(g.nu + 2) : f0);
+    f1 = f1 < T(-2) ? T(-2) : (f1 > T(g.nu + 2) ? T(g.nu + 2) : f1);
+    k0 = max((int)f0, 0);
+    k1 = min((int)f1, g.nu - 1);
+    return k0 <= k1;
+}
+
+// ---------------------------------------------------------------------------------------
+// Back projection, gather form: one thread per pixel loops over all views and the elements
+// of its footprint, accumulating  W * p  (no atomics).  The same cell atoms as the forward
+// kernel give bit-identical entries.
+// ---------------------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) back2d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
+                                                  int B, int b_off, T scale, int accumulate) {
+    const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const T X0 = GeoT<T>::x0(g) + ix * GeoT<T>::a(g), X1 = X0 + GeoT<T>::a(g);
+    const T Y0 = GeoT<T>::y0(g) + iy * GeoT<T>::b(g), Y1 = Y0 + GeoT<T>::b(g);
+    using L = typename LineOf<T>::type;
+    T acc[NB];
+#pragma unroll
+    for (int i = 0; i < NB; ++i) acc[i] = T(0);
+    for (int v = 0; v < g.n_views; ++v) {
+        int k0, k1;
+        if (!pixel_elements<T>(g, v, X0, X1, Y0, Y1, k0, k1)) continue;
+        const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+        const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
+        L l;
+        l.load(g, v, k0, w);
+        T y0, y1;
+        l.offsets(c, y0, y1);
+        T prev = cell_below(y0, y1, inv_of<T>(g, v, k0));
+        for (int k = k0; k <= k1; ++k) {
+            l.load(g, v, k + 1, w);
+            l.offsets(c, y0, y1);
+            const T cur = cell_below(y0, y1, inv_of<T>(g, v, k + 1));
+            const T wt = sigma > 0 ? cur - prev : prev - cur;
+            prev = cur;
+            if (wt != T(0)) fma_cell<T, NB>(acc, wt, ps + ((size_t)v * g.nu + k) * NB);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NB; ++i) {
+        const int b = b_off + i;
+        if (b < B) store_any<T>(x, ((size_t)b * g.ny + iy) * g.nx + ix, xdt, acc[i] * scale, accumulate != 0);
+    }
+}
+
+// Number of (pixel, view, element) with a positive FP32 area.
+__global__ void __launch_bounds__(256) nnz2d_kernel(Geo g, unsigned long long* counter) {
+    const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
+    unsigned long long cnt = 0;
+    if (ix < g.nx && iy < g.ny) {
+        const float X0 = g.x0 + ix * g.a, X1 = X0 + g.a, Y0 = g.y0 + iy * g.b, Y1 = Y0 + g.b;
+        for (int v = 0; v < g.n_views; ++v) {
+            int k0, k1;
+            if (!pixel_elements<float>(g, v, X0, X1, Y0, Y1, k0, k1)) continue;
+            const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+            const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
+            LineF l;
+            l.load(g, v, k0, w);
+            float y0, y1;
+            l.offsets(c, y0, y1);
+            float prev = cell_below(y0, y1, inv_of<float>(g, v, k0));
+            for (int k = k0; k <= k1; ++k) {
+                l.load(g, v, k + 1, w);
+                l.offsets(c, y0, y1);
+                const float cur = cell_below(y0, y1, inv_of<float>(g, v, k + 1));
+                const float wt = sigma > 0 ? cur - prev : prev - cur;
+                prev = cur;
+                cnt += wt > 0.0f;
+            }
+        }
+    }
+    // warp reduce then one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if ((threadIdx.x + 16 * threadIdx.y) % 32 == 0 && cnt) atomicAdd(counter, cnt);
+}
+
+// ---------------------------------------------------------------------------------------
+// Host dispatch
+// ---------------------------------------------------------------------------------------
+template <typename T, int NB>
+static csm_status run_forward(const csm_geom_s* gh, const void* x, void* p, int64_t batch, csm_dtype xdt,
+                              csm_dtype pdt, int flags, void* ws, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    const size_t half = al256((size_t)gh->nx * gh->ny * NB * sizeof(T));
+    T* xs0 = (T*)ws;
+    T* xs1 = (T*)((char*)ws + half);
+    const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1) : T(gh->a * gh->b);
+    for (int64_t b0 = 0; b0 < batch; b0 += NB) {
+        dim3 pb(32, 8), pg((gh->nx + 31) / 32, (gh->ny + 31) / 32);
+        prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
+        dim3 fb(128), fg((gh->nu + 127) / 128, gh->n_views);
+        fwd2d_ray<T, NB><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+                                           (flags & CSM_ACCUMULATE) ? 1 : 0);
+        csm_status e = check_launch();
+        if (e != CSM_OK) return e;
+    }
+    return CSM_OK;
+}
+
+template <typename T, int NB>
+static csm_status run_back(const csm_geom_s* gh, const void* p, void* x, int64_t batch, csm_dtype pdt,
+                           csm_dtype xdt, int flags, void* ws, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    T* ps = (T*)ws;
+    const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1) : T(gh->a * gh->b);
+    const size_t n = (size_t)gh->n_views * gh->nu;
+    for (int64_t b0 = 0; b0 < batch; b0 += NB) {
+        prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (int)pdt, (int)batch, (int)b0,
+                                                                         gh->n_views, gh->nu, ps);
+        dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16);
+        back2d_vox<T, NB><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
+                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
+        csm_status e = check_launch();
+        if (e != CSM_OK) return e;
+    }
+    return CSM_OK;
+}
+
+template <typename T>
+static csm_status fwd_nb(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt, csm_dtype pdt,
+                         int flags, void* ws, cudaStream_t st) {
+    switch (chunk_for(batch)) {
+        case 16: return run_forward<T, 16>(g, x, p, batch, xdt, pdt, flags, ws, st);
+        case 8: return run_forward<T, 8>(g, x, p, batch, xdt, pdt, flags, ws, st);
+        case 4: return run_forward<T, 4>(g, x, p, batch, xdt, pdt, flags, ws, st);
+        case 2: return run_forward<T, 2>(g, x, p, batch, xdt, pdt, flags, ws, st);
+        default: return run_forward<T, 1>(g, x, p, batch, xdt, pdt, flags, ws, st);
+    }
+}
+
+template <typename T>
+static csm_status back_nb(const csm_geom_s* g, const void* p, void* x, int64_t batch, csm_dtype pdt, csm_dtype xdt,
+                          int flags, void* ws, cudaStream_t st) {
+    switch (chunk_for(batch)) {
+        case 16: return run_back<T, 16>(g, p, x, batch, pdt, xdt, flags, ws, st);
+        case 8: return run_back<T, 8>(g, p, x, batch, pdt, xdt, flags, ws, st);
+        case 4: return run_back<T, 4>(g, p, x, batch, pdt, xdt, flags, ws, st);
+        case 2: return run_back<T, 2>(g, p, x, batch, pdt, xdt, flags, ws, st);
+        default: return run_back<T, 1>(g, p, x, batch, pdt, xdt, flags, ws, st);
+    }
+}
+
+csm_status forward_2d(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt, csm_dtype pdt,
+                      int flags, void* ws, size_t ws_bytes, cudaStream_t st) {
+    const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
+    if (flags & CSM_VOXEL_DRIVEN) return CSM_EUNSUPPORTED;
+    if (!ws || ws_bytes < workspace_2d(g, 0, batch, dbl)) return CSM_EINVAL;
+    return dbl ? fwd_nb<double>(g, x, p, batch, xdt, pdt, flags, ws, st)
+               : fwd_nb<float>(g, x, p, batch, xdt, pdt, flags, ws, st);
+}
+
+csm_status back_2d(const csm_geom_s* g, const void* p, void* x, int64_t batch, csm_dtype pdt, csm_dtype xdt,
+                   int flags, void* ws, size_t ws_bytes, cudaStream_t st) {
+    const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
+    if (!ws || ws_bytes < workspace_2d(g, 1, batch, dbl)) return CSM_EINVAL;
+    return dbl ? back_nb<double>(g, p, x, batch, pdt, xdt, flags, ws, st)
+               : back_nb<float>(g, p, x, batch, pdt, xdt, flags, ws, st);
+}
+
+csm_status nnz_2d(const csm_geom_s* gh, int64_t* out, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    cudaError_t e = cudaMemsetAsync(gh->t.counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16);
+    nnz2d_kernel<<<bg, bb, 0, st>>>(g, gh->t.counter);
+    csm_status s = check_launch();
+    if (s != CSM_OK) return s;
+    unsigned long long h = 0;
+    e = cudaMemcpyAsync(&h, gh->t.counter, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    *out = (int64_t)h;
+    return CSM_OK;
+}
+
+}  // namespace csm
