@@ -122,8 +122,9 @@ csm_status csm_back(csm_geom_t geom, const void* p, void* x, int64_t batch,
                     csm_dtype p_dt, csm_dtype x_dt, int flags,
                     void* workspace, size_t workspace_bytes, void* cuda_stream);
 
-/* Number of nonzero entries of W for this geometry (voxel, view, element with a positive
- * intersection), computed once on the device and cached.  Synchronises the stream. */
+/* Number of nonzero entries of W for this geometry: (voxel, view, element) whose
+ * intersection exceeds 1e-6 of the voxel's area / volume (the resolution of the FP32
+ * evaluation), computed once on the device and cached.  Synchronises the stream. */
 csm_status csm_nnz(csm_geom_t geom, int64_t* nnz, void* cuda_stream);
 
 /* Waits for the stream and reports an asynchronous kernel failure as CSM_ECUDA. */

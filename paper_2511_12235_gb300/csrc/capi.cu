@@ -40,6 +40,7 @@ Geo make_geo(const csm_geom_s* g) {
     o.axis_sigma = g->t.axis_sigma; o.cs_f = g->t.cs_f; o.cs_d = g->t.cs_d;
     o.line_fx = g->t.line_fx; o.line_d = g->t.line_d; o.inv_f = g->t.inv_f; o.inv_d = g->t.inv_d;
     o.wrange = g->t.wrange; o.rowq_f = g->t.rowq_f; o.rowq_d = g->t.rowq_d;
+    o.rowp_fx = g->t.rowp_fx; o.rowp_d = g->t.rowp_d;
     return o;
 }
 
@@ -168,6 +169,27 @@ static csm_status build_tables(csm_geom_s* g) {
         rowq_d[l] = vv / D;
         rowq_f[l] = (float)(vv / D);
     }
+    // row planes z = q_l t(P): height above the grid bottom at column centres, units of c
+    const size_t nrp = g->dim == 3 ? 3 * (size_t)V * (nv + 1) : 3;
+    std::vector<long long> rowp_fx(nrp, 0);
+    std::vector<double> rowp_d(nrp, 0.0);
+    if (g->dim == 3) {
+        const double zb = -0.5 * g->nz * g->c;
+        for (int v = 0; v < V; ++v) {
+            const double c = cos(g->angles[v]), sn = sin(g->angles[v]);
+            const double t00 = s - (x0 + 0.5 * g->a) * c - (y0 + 0.5 * g->b) * sn;
+            for (int l = 0; l <= nv; ++l) {
+                const double q = rowq_d[l];
+                const double A = (q * t00 - zb) / g->c, Bx = -q * g->a * c / g->c, Cy = -q * g->b * sn / g->c;
+                const size_t e = 3 * ((size_t)v * (nv + 1) + l);
+                rowp_d[e] = A; rowp_d[e + 1] = Bx; rowp_d[e + 2] = Cy;
+                if (fabs(A) + fabs(Bx) * g->nx + fabs(Cy) * g->ny > kFar) return CSM_EGEOM;
+                rowp_fx[e] = llround(A * 4294967296.0);
+                rowp_fx[e + 1] = llround(Bx * 4294967296.0);
+                rowp_fx[e + 2] = llround(Cy * 4294967296.0);
+            }
+        }
+    }
 
     // one device block for everything
     auto al = [](size_t n) { return (n + 255) & ~(size_t)255; };
@@ -182,6 +204,8 @@ static csm_status build_tables(csm_geom_s* g) {
     size_t o_wr = off; off += al(wrange.size() * sizeof(int));
     size_t o_rf = off; off += al(rowq_f.size() * sizeof(float));
     size_t o_rd = off; off += al(rowq_d.size() * sizeof(double));
+    size_t o_pfx = off; off += al(rowp_fx.size() * sizeof(long long));
+    size_t o_pd = off; off += al(rowp_d.size() * sizeof(double));
     size_t o_cnt = off; off += al(sizeof(unsigned long long));
     std::vector<char> host(off, 0);
     memcpy(&host[o_as], axis_sigma.data(), axis_sigma.size() * sizeof(int));
@@ -194,6 +218,8 @@ static csm_status build_tables(csm_geom_s* g) {
     memcpy(&host[o_wr], wrange.data(), wrange.size() * sizeof(int));
     memcpy(&host[o_rf], rowq_f.data(), rowq_f.size() * sizeof(float));
     memcpy(&host[o_rd], rowq_d.data(), rowq_d.size() * sizeof(double));
+    memcpy(&host[o_pfx], rowp_fx.data(), rowp_fx.size() * sizeof(long long));
+    memcpy(&host[o_pd], rowp_d.data(), rowp_d.size() * sizeof(double));
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, off);
     if (e != cudaSuccess) { set_cuda_error(e); return e == cudaErrorMemoryAllocation ? CSM_ENOMEM : CSM_ECUDA; }
@@ -211,6 +237,8 @@ static csm_status build_tables(csm_geom_s* g) {
     g->t.wrange = (int*)(b + o_wr);
     g->t.rowq_f = (float*)(b + o_rf);
     g->t.rowq_d = (double*)(b + o_rd);
+    g->t.rowp_fx = (long long*)(b + o_pfx);
+    g->t.rowp_d = (double*)(b + o_pd);
     g->t.counter = (unsigned long long*)(b + o_cnt);
     return CSM_OK;
 }
@@ -225,7 +253,12 @@ static csm_status finish_create(csm_geom_s* g, const double* angles, csm_geom_t*
     double hz = g->dim == 3 ? 0.5 * g->nz * g->c : 0.0;
     double r = sqrt(pow(0.5 * g->nx * g->a, 2) + pow(0.5 * g->ny * g->b, 2));
     if (!(g->s > r) || !(g->sdd > g->s)) return CSM_EGEOM;
-    (void)hz;
+    if (g->dim == 3) {
+        // detector rows one voxel can reach in one view: its v-extent at the nearest depth
+        double tmin = g->s - r, diag = sqrt(g->a * g->a + g->b * g->b);
+        double vext = g->sdd * (g->c / tmin + hz * diag / (tmin * tmin));
+        if (vext / g->dv + 3.0 > (double)kMaxRowCorners) return CSM_EUNSUPPORTED;
+    }
     cudaError_t e = cudaGetDevice(&g->device);
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     csm_status st = build_tables(g);

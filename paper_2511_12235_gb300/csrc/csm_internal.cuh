@@ -25,7 +25,10 @@ namespace csm {
 //   line_d      = the same two numbers in double
 //   inv2        = 1 / (2 |step|) per corner (float and double)
 //   wrange      = per element k: the walk cells [w0, w1) where its strip meets the grid
-//   rows (3D)   = per row corner l: q_l = v_l / sdd (float and double)
+//   rows (3D)   = per row corner l: q_l = v_l / sdd (float and double), and per view the
+//                 height of the plane { v(P) = v_l } = { z = q_l t(P) } above the grid's
+//                 bottom face at the centre of column (ix, iy), in units of c:
+//                     G_l(ix, iy) = A + ix B + iy C   (32.32 fixed point and double)
 // ---------------------------------------------------------------------------------------
 struct DeviceTables {
     int* axis_sigma = nullptr;     // [V][2]
@@ -38,6 +41,8 @@ struct DeviceTables {
     int* wrange = nullptr;         // [V][nu][2]
     float* rowq_f = nullptr;       // [nv+1]
     double* rowq_d = nullptr;      // [nv+1]
+    long long* rowp_fx = nullptr;  // [V][nv+1][3] row planes, 32.32 fixed point (3D)
+    double* rowp_d = nullptr;      // [V][nv+1][3]
     unsigned long long* counter = nullptr;  // scratch word for csm_nnz
 };
 
@@ -77,9 +82,15 @@ struct Geo {
     const int* wrange;
     const float* rowq_f;
     const double* rowq_d;
+    const long long* rowp_fx;
+    const double* rowp_d;
 };
 
 Geo make_geo(const csm_geom_s* g);
+
+// Most detector row corners (rows + 1) that one voxel's footprint can span in one view; the
+// 3D kernels keep one value per corner in registers.  Geometries beyond it are refused.
+constexpr int kMaxRowCorners = 8;
 
 // thread-local record of the last CUDA error text
 void set_cuda_error(cudaError_t e);

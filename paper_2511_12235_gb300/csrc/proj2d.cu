@@ -66,59 +66,72 @@ __device__ __forceinline__ void store_any(void* base, size_t i, int dt, T v, boo
     }
 }
 
-// x[b][iy][ix] -> xs0[(ix*ny + iy)*NB + bb] (walk x) and xs1[(iy*nx + ix)*NB + bb] (walk y)
+// Batch items are grouped in vectors of VW = min(NB, 4); a chunk of NB items is stored as
+// Q = NB / VW planes so that the lanes of a warp, which visit neighbouring cells, read
+// neighbouring 16-byte vectors:
+//   walk x:  xs0[((ix * Q + q) * ny + iy) * VW + r]      (b = q * VW + r)
+//   walk y:  xs1[((iy * Q + q) * nx + ix) * VW + r]
+template <int NB> struct Vec { static constexpr int W = NB < 4 ? NB : 4; static constexpr int Q = NB / W; };
+
 template <typename T, int NB>
 __global__ void __launch_bounds__(256) prep_image_2d(const void* __restrict__ x, int xdt, int B, int b_off,
                                                      int nx, int ny, T* __restrict__ xs0, T* __restrict__ xs1) {
+    constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
     __shared__ T tile[32][33];
     const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int bb = 0; bb < NB; ++bb) {
-        const int b = b_off + bb;
+        const int b = b_off + bb, q = bb / VW, r = bb % VW;
         for (int j = ty; j < 32; j += 8) {
             int ix = bx + tx, iy = by + j;
             T val = T(0);
             if (ix < nx && iy < ny && b < B) val = load_any<T>(x, ((size_t)b * ny + iy) * nx + ix, xdt);
             tile[j][tx] = val;
-            if (ix < nx && iy < ny) xs1[((size_t)iy * nx + ix) * NB + bb] = val;
+            if (ix < nx && iy < ny) xs1[(((size_t)iy * Q + q) * nx + ix) * VW + r] = val;
         }
         __syncthreads();
         for (int j = ty; j < 32; j += 8) {
             int ix = bx + j, iy = by + tx;
-            if (ix < nx && iy < ny) xs0[((size_t)ix * ny + iy) * NB + bb] = tile[tx][j];
+            if (ix < nx && iy < ny) xs0[(((size_t)ix * Q + q) * ny + iy) * VW + r] = tile[tx][j];
         }
         __syncthreads();
     }
 }
 
-// p[b][v][k] -> ps[(v*nu + k)*NB + bb]
+// p[b][v][k] -> ps[((v * Q + q) * nu + k) * VW + r]
 template <typename T, int NB>
 __global__ void prep_sino_2d(const void* __restrict__ p, int pdt, int B, int b_off, int V, int nu,
                              T* __restrict__ ps) {
+    constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)V * nu) return;
+    const size_t v = i / nu, k = i % nu;
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb) {
         const int b = b_off + bb;
-        ps[i * NB + bb] = b < B ? load_any<T>(p, (size_t)b * V * nu + i, pdt) : T(0);
+        ps[((v * Q + bb / VW) * nu + k) * VW + bb % VW] = b < B ? load_any<T>(p, (size_t)b * V * nu + i, pdt) : T(0);
     }
 }
 
+// acc[b] += wt * value[b] for the NB items of one cell; `base` points at the cell's first
+// vector and consecutive planes are `plane` elements apart.
 template <typename T, int NB>
-__device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict__ xp) {
-    if constexpr (sizeof(T) == 4 && NB % 4 == 0) {
-        const float4* q = reinterpret_cast<const float4*>(xp);
+__device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict__ base, size_t plane) {
+    constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
+    if constexpr (sizeof(T) == 4 && VW == 4) {
 #pragma unroll
-        for (int i = 0; i < NB / 4; ++i) {
-            float4 v = __ldg(q + i);
-            acc[4 * i + 0] += wt * v.x;
-            acc[4 * i + 1] += wt * v.y;
-            acc[4 * i + 2] += wt * v.z;
-            acc[4 * i + 3] += wt * v.w;
+        for (int q = 0; q < Q; ++q) {
+            float4 v = __ldg(reinterpret_cast<const float4*>(base + q * plane));
+            acc[4 * q + 0] += wt * v.x;
+            acc[4 * q + 1] += wt * v.y;
+            acc[4 * q + 2] += wt * v.z;
+            acc[4 * q + 3] += wt * v.w;
         }
     } else {
 #pragma unroll
-        for (int i = 0; i < NB; ++i) acc[i] += wt * __ldg(xp + i);
+        for (int q = 0; q < Q; ++q)
+#pragma unroll
+            for (int r = 0; r < VW; ++r) acc[q * VW + r] += wt * __ldg(base + q * plane + r);
     }
 }
 
@@ -128,7 +141,7 @@ __device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict
 // its two corner lines and accumulates  W * x  for NB batch items.
 // ---------------------------------------------------------------------------------------
 template <typename T, int NB>
-__global__ void __launch_bounds__(128) fwd2d_ray(Geo g, const T* __restrict__ xs0, const T* __restrict__ xs1,
+__global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0, const T* __restrict__ xs1,
                                                  void* __restrict__ p, int pdt, int B, int b_off, T scale,
                                                  int accumulate) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -157,7 +170,7 @@ __global__ void __launch_bounds__(128) fwd2d_ray(Geo g, const T* __restrict__ xs
             lb.offsets(c, b0, b1);
             const T fa = cell_below(a0, a1, ia), fb = cell_below(b0, b1, ib);
             const T wt = sigma > 0 ? fb - fa : fa - fb;
-            if (wt != T(0)) fma_cell<T, NB>(acc, wt, xs + ((size_t)w * nc + c) * NB);
+            if (wt != T(0)) fma_cell<T, NB>(acc, wt, xs + ((size_t)w * Vec<NB>::Q * nc + c) * Vec<NB>::W, (size_t)nc * Vec<NB>::W);
         }
         la.step();
         lb.step();
@@ -229,48 +242,71 @@ __device__ __forceinline__ bool pixel_elements(const Geo& g, int v, T X0, T X1, 
 }
 
 // ---------------------------------------------------------------------------------------
-// Back projection, gather form: one thread per pixel loops over all views and the elements
-// of its footprint, accumulating  W * p  (no atomics).  The same cell atoms as the forward
-// kernel give bit-identical entries.
+// Back projection, gather form: each pixel's views are split over BG thread groups of one
+// block (views v = g, g + BG, ...); each thread loops over its views and the elements of its
+// footprint accumulating  W * p  in registers, then the groups' partial sums are added in
+// shared memory in a fixed order (deterministic, no atomics).  The same cell atoms as the
+// forward kernel give bit-identical entries.
 // ---------------------------------------------------------------------------------------
+constexpr int BTX = 16, BTY = 4, BG = 4;   // pixel tile 16 x 4, 4 view groups: 256 threads
+
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) back2d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
-                                                  int B, int b_off, T scale, int accumulate) {
-    const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
-    if (ix >= g.nx || iy >= g.ny) return;
-    const T X0 = GeoT<T>::x0(g) + ix * GeoT<T>::a(g), X1 = X0 + GeoT<T>::a(g);
-    const T Y0 = GeoT<T>::y0(g) + iy * GeoT<T>::b(g), Y1 = Y0 + GeoT<T>::b(g);
-    using L = typename LineOf<T>::type;
+__global__ void __launch_bounds__(BTX * BTY * BG) back2d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x,
+                                                           int xdt, int B, int b_off, T scale, int accumulate) {
+    constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
+    __shared__ T part[BG - 1][BTX * BTY][NB];
+    const int ix = blockIdx.x * BTX + threadIdx.x, iy = blockIdx.y * BTY + threadIdx.y;
+    const int grp = threadIdx.z;
+    const bool inside = ix < g.nx && iy < g.ny;
     T acc[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) acc[i] = T(0);
-    for (int v = 0; v < g.n_views; ++v) {
-        int k0, k1;
-        if (!pixel_elements<T>(g, v, X0, X1, Y0, Y1, k0, k1)) continue;
-        const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
-        const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
-        L l;
-        l.load(g, v, k0, w);
-        T y0, y1;
-        l.offsets(c, y0, y1);
-        T prev = cell_below(y0, y1, inv_of<T>(g, v, k0));
-        for (int k = k0; k <= k1; ++k) {
-            l.load(g, v, k + 1, w);
+    if (inside) {
+        const T X0 = GeoT<T>::x0(g) + ix * GeoT<T>::a(g), X1 = X0 + GeoT<T>::a(g);
+        const T Y0 = GeoT<T>::y0(g) + iy * GeoT<T>::b(g), Y1 = Y0 + GeoT<T>::b(g);
+        using L = typename LineOf<T>::type;
+        const size_t plane = (size_t)g.nu * VW;
+        for (int v = grp; v < g.n_views; v += BG) {
+            int k0, k1;
+            if (!pixel_elements<T>(g, v, X0, X1, Y0, Y1, k0, k1)) continue;
+            const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+            const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
+            L l;
+            l.load(g, v, k0, w);
+            T y0, y1;
             l.offsets(c, y0, y1);
-            const T cur = cell_below(y0, y1, inv_of<T>(g, v, k + 1));
-            const T wt = sigma > 0 ? cur - prev : prev - cur;
-            prev = cur;
-            if (wt != T(0)) fma_cell<T, NB>(acc, wt, ps + ((size_t)v * g.nu + k) * NB);
+            T prev = cell_below(y0, y1, inv_of<T>(g, v, k0));
+            const T* pv = ps + (size_t)v * Q * plane;
+            for (int k = k0; k <= k1; ++k) {
+                l.load(g, v, k + 1, w);
+                l.offsets(c, y0, y1);
+                const T cur = cell_below(y0, y1, inv_of<T>(g, v, k + 1));
+                const T wt = sigma > 0 ? cur - prev : prev - cur;
+                prev = cur;
+                if (wt != T(0)) fma_cell<T, NB>(acc, wt, pv + (size_t)k * VW, plane);
+            }
         }
     }
+    const int pix = threadIdx.y * BTX + threadIdx.x;
+    if (grp > 0) {
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        const int b = b_off + i;
-        if (b < B) store_any<T>(x, ((size_t)b * g.ny + iy) * g.nx + ix, xdt, acc[i] * scale, accumulate != 0);
+        for (int i = 0; i < NB; ++i) part[grp - 1][pix][i] = acc[i];
+    }
+    __syncthreads();
+    if (grp == 0 && inside) {
+#pragma unroll
+        for (int gg = 0; gg < BG - 1; ++gg)
+#pragma unroll
+            for (int i = 0; i < NB; ++i) acc[i] += part[gg][pix][i];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const int b = b_off + i;
+            if (b < B) store_any<T>(x, ((size_t)b * g.ny + iy) * g.nx + ix, xdt, acc[i] * scale, accumulate != 0);
+        }
     }
 }
 
-// Number of (pixel, view, element) with a positive FP32 area.
+// Number of (pixel, view, element) whose area exceeds 1e-6 of the pixel's.
 __global__ void __launch_bounds__(256) nnz2d_kernel(Geo g, unsigned long long* counter) {
     const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
     unsigned long long cnt = 0;
@@ -292,7 +328,7 @@ __global__ void __launch_bounds__(256) nnz2d_kernel(Geo g, unsigned long long* c
                 const float cur = cell_below(y0, y1, inv_of<float>(g, v, k + 1));
                 const float wt = sigma > 0 ? cur - prev : prev - cur;
                 prev = cur;
-                cnt += wt > 0.0f;
+                cnt += wt > 1e-6f;   // above 1e-6 of the pixel area (FP32 resolves it)
             }
         }
     }
@@ -315,7 +351,7 @@ static csm_status run_forward(const csm_geom_s* gh, const void* x, void* p, int6
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 pb(32, 8), pg((gh->nx + 31) / 32, (gh->ny + 31) / 32);
         prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
-        dim3 fb(128), fg((gh->nu + 127) / 128, gh->n_views);
+        dim3 fb(64), fg((gh->nu + 63) / 64, gh->n_views);
         fwd2d_ray<T, NB><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
@@ -334,7 +370,7 @@ static csm_status run_back(const csm_geom_s* gh, const void* p, void* x, int64_t
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (int)pdt, (int)batch, (int)b0,
                                                                          gh->n_views, gh->nu, ps);
-        dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16);
+        dim3 bb(BTX, BTY, BG), bg((gh->nx + BTX - 1) / BTX, (gh->ny + BTY - 1) / BTY);
         back2d_vox<T, NB><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
                                             (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();

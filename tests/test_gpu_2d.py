@@ -133,14 +133,12 @@ def test_half_storage(csm, dt, bound):
 
 
 def test_nnz_matches_oracle(csm):
-    """nnz counts entries whose FP32 area is positive: it lies between the oracle's count of
-    entries above 1e-6 of a pixel (FP32 resolves those) and its count of all positive ones
-    (FP64 also keeps slivers far below FP32 resolution)."""
+    """nnz counts entries above 1e-6 of the pixel area, evaluated in FP32 (error ~1e-7 of
+    a pixel): it lies between the oracle's counts above 1.5e-6 and above 0.5e-6."""
     g = synth.config("fan2d_64")
     rows, cols, vals = oracle.coo(g)
-    P = csm.Projector(g)
-    n = P.nnz()
-    assert int(np.sum(vals > 1e-6)) <= n <= len(vals), (n, int(np.sum(vals > 1e-6)), len(vals))
+    n = csm.Projector(g).nnz()
+    assert int(np.sum(vals > 1.5e-6)) <= n <= int(np.sum(vals > 0.5e-6)), (n, len(vals))
 
 
 def test_fan512_batch16_sampled_views(csm):
