@@ -127,6 +127,31 @@ csm_status csm_back(csm_geom_t geom, const void* p, void* x, int64_t batch,
  * evaluation), computed once on the device and cached.  Synchronises the stream. */
 csm_status csm_nnz(csm_geom_t geom, int64_t* nnz, void* cuda_stream);
 
+/* ---- vector kernels of the reconstruction solvers -------------------------------------
+ * The paper reconstructs by Nesterov's accelerated gradient on the Tikhonov objective with W
+ * normalised by its spectral norm from 100 power iterations (Section "Numerical
+ * Experiments", Eq. (exp_tikh)), and names the conjugate-gradient method in the same
+ * section.  These kernels keep every scalar of such an iteration in device memory. */
+
+/* Bytes of workspace csm_dot needs for `batch` inner products. */
+csm_status csm_dot_workspace_bytes(int64_t batch, size_t* bytes);
+
+/* out[b] = sum_i a[b n + i] * c[b n + i] for b < batch (1 <= batch <= 65535): FP64
+ * accumulation, fixed summation order (bit-reproducible).  a, c: device arrays of dtype dt;
+ * out: device array of `batch` doubles; workspace: device scratch of
+ * csm_dot_workspace_bytes(batch) bytes, contents on return unspecified. */
+csm_status csm_dot(const void* a, const void* c, int64_t n, int64_t batch, csm_dtype dt,
+                   double* out, void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* y[b n + i] = A_b x[b n + i] + B_b y[b n + i] with per-item coefficients
+ *   A_b = a_c * a_num[b] / a_den[b],  B_b = b_c * b_num[b] / b_den[b]
+ * where a NULL num / den device pointer stands for 1 and a zero denominator gives 0.
+ * flags bit 0 (bit 1): use sqrt(a_den[b]) (sqrt(b_den[b])).  x may be NULL (then A_b x = 0);
+ * when B_b is 0, y is not read.  In place on y (dtype dt). */
+csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const double* a_num,
+                     const double* a_den, const void* x, double b_c, const double* b_num,
+                     const double* b_den, void* y, int flags, void* cuda_stream);
+
 /* Waits for the stream and reports an asynchronous kernel failure as CSM_ECUDA. */
 csm_status csm_sync_status(void* cuda_stream);
 

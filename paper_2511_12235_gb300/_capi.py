@@ -59,6 +59,14 @@ lib.csm_back.argtypes = [csm_geom_t, C.c_void_p, C.c_void_p, C.c_int64, C.c_int,
 lib.csm_back.restype = _st
 lib.csm_nnz.argtypes = [csm_geom_t, C.POINTER(C.c_int64), C.c_void_p]
 lib.csm_nnz.restype = _st
+lib.csm_dot_workspace_bytes.argtypes = [C.c_int64, C.POINTER(C.c_size_t)]
+lib.csm_dot_workspace_bytes.restype = _st
+lib.csm_dot.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
+                        C.c_void_p]
+lib.csm_dot.restype = _st
+lib.csm_axpby.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+lib.csm_axpby.restype = _st
 lib.csm_sync_status.argtypes = [C.c_void_p]
 lib.csm_sync_status.restype = _st
 lib.csm_status_string.argtypes = [_st]
@@ -69,7 +77,7 @@ lib.csm_last_cuda_error.restype = C.c_char_p
 EXPORTED = [
     "csm_geom_create_2d", "csm_geom_create_3d", "csm_geom_free", "csm_workspace_bytes",
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
-    "csm_last_cuda_error",
+    "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby",
 ]
 
 
@@ -126,3 +134,18 @@ def csm_nnz(h, stream) -> int:
 
 def csm_sync_status(stream) -> None:
     check(lib.csm_sync_status(stream), "csm_sync_status")
+
+
+def csm_dot_workspace_bytes(batch: int) -> int:
+    n = C.c_size_t()
+    check(lib.csm_dot_workspace_bytes(batch, C.byref(n)), "csm_dot_workspace_bytes")
+    return n.value
+
+
+def csm_dot(a_ptr, c_ptr, n, batch, dt, out_ptr, ws_ptr, ws_bytes, stream) -> None:
+    check(lib.csm_dot(a_ptr, c_ptr, n, batch, dt, out_ptr, ws_ptr, ws_bytes, stream), "csm_dot")
+
+
+def csm_axpby(n, batch, dt, a_c, a_num, a_den, x_ptr, b_c, b_num, b_den, y_ptr, flags, stream) -> None:
+    check(lib.csm_axpby(n, batch, dt, a_c, a_num, a_den, x_ptr, b_c, b_num, b_den, y_ptr, flags, stream),
+          "csm_axpby")

@@ -1,0 +1,146 @@
+// vecops.cu -- batched vector kernels for the reconstruction solvers (CG least squares,
+// Nesterov's accelerated gradient on the Tikhonov objective, power iteration for ||W||;
+// Section "Numerical Experiments", Eq. (exp_tikh)).  Scalars that the iterations derive from
+// inner products stay in device memory, so a whole iteration can be captured in a CUDA graph.
+#include "csm_internal.cuh"
+
+namespace csm {
+
+constexpr int kDotBlocks = 256;    // partial sums per batch item (first stage)
+constexpr int kDotThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ double ld(const void* p, size_t i, int dt) {
+    switch (dt) {
+        case CSM_F64: return ((const double*)p)[i];
+        case CSM_BF16: return (double)__bfloat162float(((const __nv_bfloat16*)p)[i]);
+        case CSM_F16: return (double)__half2float(((const __half*)p)[i]);
+        default: return (double)((const float*)p)[i];
+    }
+}
+
+// Stage 1: block (j, b) sums a[b, i] * b[b, i] over a grid-stride range of i in FP64.
+__global__ void __launch_bounds__(kDotThreads) dot_partial(const void* __restrict__ a, const void* __restrict__ b,
+                                                           int dt, int64_t n, double* __restrict__ part) {
+    const int bb = blockIdx.y;
+    const size_t off = (size_t)bb * n;
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * kDotThreads + threadIdx.x; i < n; i += (int64_t)kDotBlocks * kDotThreads)
+        s += ld<double>(a, off + i, dt) * ld<double>(b, off + i, dt);
+    __shared__ double red[kDotThreads];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(size_t)bb * kDotBlocks + blockIdx.x] = red[0];
+}
+
+// Stage 2: one block per batch item adds its partials in a fixed order.
+__global__ void __launch_bounds__(kDotThreads) dot_final(const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double red[kDotThreads];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < kDotBlocks; j += kDotThreads) s += part[(size_t)blockIdx.x * kDotBlocks + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = kDotThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[blockIdx.x] = red[0];
+}
+
+__device__ __forceinline__ double coeff(double c, const double* num, const double* den, int b, bool den_sqrt) {
+    double v = c;
+    if (num) v *= num[b];
+    if (den) {
+        double d = den_sqrt ? sqrt(den[b]) : den[b];
+        v = d != 0.0 ? v / d : 0.0;
+    }
+    return v;
+}
+
+// y[b, i] = A_b x[b, i] + B_b y[b, i]
+__global__ void axpby_kernel(int64_t n, int64_t batch, int dt, double ac, const double* __restrict__ an,
+                             const double* __restrict__ ad, const void* __restrict__ x, double bc,
+                             const double* __restrict__ bn, const double* __restrict__ bd, void* __restrict__ y,
+                             int den_sqrt) {
+    const int b = blockIdx.y;
+    const double A = coeff(ac, an, ad, b, den_sqrt & 1), B = coeff(bc, bn, bd, b, den_sqrt & 2);
+    const size_t off = (size_t)b * n;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        switch (dt) {
+            case CSM_F64: {
+                double* q = (double*)y + off + i;
+                const double xv = x ? ((const double*)x)[off + i] : 0.0;
+                *q = A * xv + (B != 0.0 ? B * *q : 0.0);
+                break;
+            }
+            case CSM_F32: {
+                float* q = (float*)y + off + i;
+                const float xv = x ? ((const float*)x)[off + i] : 0.0f;
+                *q = (float)A * xv + (B != 0.0 ? (float)B * *q : 0.0f);
+                break;
+            }
+            case CSM_BF16: {
+                __nv_bfloat16* q = (__nv_bfloat16*)y + off + i;
+                const float xv = x ? __bfloat162float(((const __nv_bfloat16*)x)[off + i]) : 0.0f;
+                *q = __float2bfloat16_rn((float)A * xv + (B != 0.0 ? (float)B * __bfloat162float(*q) : 0.0f));
+                break;
+            }
+            default: {
+                __half* q = (__half*)y + off + i;
+                const float xv = x ? __half2float(((const __half*)x)[off + i]) : 0.0f;
+                *q = __float2half_rn((float)A * xv + (B != 0.0 ? (float)B * __half2float(*q) : 0.0f));
+                break;
+            }
+        }
+    }
+}
+
+size_t dot_workspace_bytes(int64_t batch) { return (size_t)batch * kDotBlocks * sizeof(double); }
+
+csm_status dot_launch(const void* a, const void* b, int64_t n, int64_t batch, csm_dtype dt, double* out,
+                      double* part, cudaStream_t st) {
+    dim3 g1(kDotBlocks, (unsigned)batch);
+    dot_partial<<<g1, kDotThreads, 0, st>>>(a, b, (int)dt, n, part);
+    dot_final<<<(unsigned)batch, kDotThreads, 0, st>>>(part, out);
+    return check_launch();
+}
+
+}  // namespace csm
+
+using namespace csm;
+
+extern "C" {
+
+csm_status csm_dot_workspace_bytes(int64_t batch, size_t* bytes) {
+    if (batch <= 0 || batch > 65535 || !bytes) return CSM_EINVAL;
+    *bytes = dot_workspace_bytes(batch);
+    return CSM_OK;
+}
+
+csm_status csm_dot(const void* a, const void* b, int64_t n, int64_t batch, csm_dtype dt, double* out,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+    if (!a || !b || !out || n < 0 || batch <= 0 || batch > 65535) return CSM_EINVAL;
+    if (dt != CSM_F32 && dt != CSM_F64 && dt != CSM_BF16 && dt != CSM_F16) return CSM_EINVAL;
+    if (!workspace || workspace_bytes < dot_workspace_bytes(batch)) return CSM_EINVAL;
+    return dot_launch(a, b, n, batch, dt, out, (double*)workspace, (cudaStream_t)stream);
+}
+
+csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const double* a_num, const double* a_den,
+                     const void* x, double b_c, const double* b_num, const double* b_den, void* y, int flags,
+                     void* stream) {
+    if (!y || n < 0 || batch <= 0 || batch > 65535) return CSM_EINVAL;
+    if (dt != CSM_F32 && dt != CSM_F64 && dt != CSM_BF16 && dt != CSM_F16) return CSM_EINVAL;
+    if (n == 0) return CSM_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 1216) blocks = 1216;   // 8 blocks of 256 per SM on 152 SMs, grid-stride beyond
+    dim3 grid((unsigned)blocks, (unsigned)batch);
+    axpby_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, batch, (int)dt, a_c, a_num, a_den, x, b_c, b_num, b_den,
+                                                        y, flags);
+    return check_launch();
+}
+
+}  // extern "C"
