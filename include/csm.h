@@ -152,6 +152,21 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
                      const double* a_den, const void* x, double b_c, const double* b_num,
                      const double* b_den, void* y, int flags, void* cuda_stream);
 
+/* csm_dot without a workspace argument, for callers that cannot allocate device memory
+ * (e.g. everything is owned by a pool allocator, a plug-in given no allocator, or a loop
+ * where the device synchronisation cudaMalloc / cudaFree may cause is not acceptable).  The
+ * paper has no counterpart: this is an interface for such callers only.  The partial sums
+ * go to a fixed 128 KiB array in the library's device memory (held on every GPU that loads
+ * the library until exit), so batch may not exceed CSM_DOT_NOALLOC_MAX_BATCH: larger
+ * batches return CSM_EINVAL.  Result and arguments otherwise as csm_dot (same kernels, same
+ * summation order).  The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.  All calls share the
+ * one array: calls that may overlap on the GPU (different streams, or different host
+ * threads) race and must be serialised by the caller.  No allocation is made. */
+#define CSM_DOT_NOALLOC_MAX_BATCH 64
+csm_status csm_dot_noalloc(const void* a, const void* c, int64_t n, int64_t batch, csm_dtype dt,
+                           double* out, void* cuda_stream);
+
 /* Waits for the stream and reports an asynchronous kernel failure as CSM_ECUDA. */
 csm_status csm_sync_status(void* cuda_stream);
 

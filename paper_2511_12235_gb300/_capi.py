@@ -67,6 +67,8 @@ lib.csm_dot.restype = _st
 lib.csm_axpby.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_double, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
 lib.csm_axpby.restype = _st
+lib.csm_dot_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]
+lib.csm_dot_noalloc.restype = _st
 lib.csm_sync_status.argtypes = [C.c_void_p]
 lib.csm_sync_status.restype = _st
 lib.csm_status_string.argtypes = [_st]
@@ -77,8 +79,9 @@ lib.csm_last_cuda_error.restype = C.c_char_p
 EXPORTED = [
     "csm_geom_create_2d", "csm_geom_create_3d", "csm_geom_free", "csm_workspace_bytes",
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
-    "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby",
+    "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
 ]
+CSM_DOT_NOALLOC_MAX_BATCH = 64
 
 
 class CsmError(RuntimeError):
@@ -149,3 +152,7 @@ def csm_dot(a_ptr, c_ptr, n, batch, dt, out_ptr, ws_ptr, ws_bytes, stream) -> No
 def csm_axpby(n, batch, dt, a_c, a_num, a_den, x_ptr, b_c, b_num, b_den, y_ptr, flags, stream) -> None:
     check(lib.csm_axpby(n, batch, dt, a_c, a_num, a_den, x_ptr, b_c, b_num, b_den, y_ptr, flags, stream),
           "csm_axpby")
+
+
+def csm_dot_noalloc(a_ptr, c_ptr, n, batch, dt, out_ptr, stream) -> None:
+    check(lib.csm_dot_noalloc(a_ptr, c_ptr, n, batch, dt, out_ptr, stream), "csm_dot_noalloc")

@@ -2,6 +2,8 @@
 // Nesterov's accelerated gradient on the Tikhonov objective, power iteration for ||W||;
 // Section "Numerical Experiments", Eq. (exp_tikh)).  Scalars that the iterations derive from
 // inner products stay in device memory, so a whole iteration can be captured in a CUDA graph.
+#include <mutex>
+
 #include "csm_internal.cuh"
 
 namespace csm {
@@ -109,6 +111,43 @@ csm_status dot_launch(const void* a, const void* b, int64_t n, int64_t batch, cs
     return check_launch();
 }
 
+// ---------------------------------------------------------------------------------------
+// Allocation-free inner products.  Some callers cannot allocate device memory for the
+// partial sums: code that has handed all device memory to a pool allocator, plug-ins that
+// are given no allocator, and latency-critical loops where cudaMalloc / cudaFree, which may
+// synchronise the device, are not acceptable.  For them the first-stage partials live in a
+// fixed array in the library's own device memory, sized for kDotNoAllocMaxBatch items
+// (128 KiB); every GPU that loads the library holds it until the process exits.
+// ---------------------------------------------------------------------------------------
+constexpr int kDotNoAllocMaxBatch = 64;
+static __device__ __align__(256) double g_dot_scratch[kDotNoAllocMaxBatch * kDotBlocks];
+
+constexpr int kMaxDevices = 64;
+static std::mutex g_scratch_mu;
+static double* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of g_dot_scratch on the current device.  In host code the array's name
+// denotes a host-side stand-in, so the address is looked up once per device (with that device
+// current) and cached.
+static csm_status dot_scratch_address(double** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    if (dev < 0 || dev >= kMaxDevices) return CSM_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_dot_scratch);
+        if (e != cudaSuccess || !p) {
+            set_cuda_error(e);
+            return CSM_ECUDA;
+        }
+        g_scratch_addr[dev] = (double*)p;
+    }
+    *out = g_scratch_addr[dev];
+    return CSM_OK;
+}
+
 }  // namespace csm
 
 using namespace csm;
@@ -141,6 +180,18 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
     axpby_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, batch, (int)dt, a_c, a_num, a_den, x, b_c, b_num, b_den,
                                                         y, flags);
     return check_launch();
+}
+
+csm_status csm_dot_noalloc(const void* a, const void* c, int64_t n, int64_t batch, csm_dtype dt, double* out,
+                           void* stream) {
+    if (!a || !c || !out || n < 0 || batch <= 0) return CSM_EINVAL;
+    if (batch > kDotNoAllocMaxBatch) return CSM_EINVAL;   // beyond the fixed scratch array
+    if (dt != CSM_F32 && dt != CSM_F64 && dt != CSM_BF16 && dt != CSM_F16) return CSM_EINVAL;
+    double* part = nullptr;
+    csm_status s = dot_scratch_address(&part);
+    if (s != CSM_OK) return s;
+    // every partial slot the second stage reads is written by the first: nothing to clear
+    return dot_launch(a, c, n, batch, dt, out, part, (cudaStream_t)stream);
 }
 
 }  // extern "C"
