@@ -28,9 +28,18 @@ METRIC = "fwd+back projector Gvoxel-ray updates/s vs FP64 oracle; served recon p
 UNIT = "Gupdates/s"
 WORKLOAD = "fan2d_512"
 BATCH = 16
-# algorithmic FP32 operations per nonzero entry: the weight (two cell atoms and their
-# difference, 12 flops) plus one multiply-add per batch item
-FLOPS_PER_ENTRY_WEIGHT = 12
+# other workloads (not the default line): batch and storage dtype
+WORKLOADS = {
+    "fan2d_512": dict(batch=16, dtype="f32"),
+    "fan2d_64": dict(batch=1, dtype="f64"),
+    "cone3d_128": dict(batch=1, dtype="f32"),
+    "cone3d_512": dict(batch=1, dtype="f32"),
+}
+# algorithmic FP32 operations per nonzero entry, plus one multiply-add per batch item:
+#   2D: two cell atoms and their difference (12 flops)
+#   3D: one Phi (two relu integrals over a top-view atom, shared by four entries) and the
+#       double difference (40 flops)
+FLOPS_PER_ENTRY_WEIGHT = {2: 12, 3: 40}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -41,6 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--dtype", default=None, choices=["f32", "f64", "bf16", "f16"],
+                    help="storage dtype of volume and sinogram (default per workload)")
     return ap.parse_args()
 
 
@@ -186,15 +198,22 @@ def run_ours(args, rank, world, local):
         import paper_2511_12235_gb300 as csm
     import synth
 
-    g = synth.config(WORKLOAD)
-    seeds = range(rank * BATCH, (rank + 1) * BATCH)
-    xs_host = np.stack([synth.ellipse_phantom(512, s) for s in seeds]).astype(np.float32)
-    x = torch.from_numpy(xs_host).to(dev)
+    wl = args.workload
+    batch = WORKLOADS[wl]["batch"]
+    sdt = args.dtype or WORKLOADS[wl]["dtype"]
+    tdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16, "f16": torch.float16}[sdt]
+    g = synth.config(wl)
+    seeds = range(rank * batch, (rank + 1) * batch)
+    if g["dim"] == 2:
+        xs_host = np.stack([synth.ellipse_phantom(g["nx"], s) for s in seeds]).astype(np.float32)
+    else:
+        xs_host = np.stack([synth.ellipsoid_phantom(g["nx"], s, dtype=np.float32) for s in seeds])
+    x = torch.from_numpy(xs_host).to(dev).to(tdt)
     P = csm.Projector(g, device=dev)
     nnz = P.nnz()
     stream = torch.cuda.current_stream(dev)
-    p = torch.empty((BATCH,) + P.sino_shape, dtype=torch.float32, device=dev)
-    xb = torch.empty((BATCH,) + P.vol_shape, dtype=torch.float32, device=dev)
+    p = torch.empty((batch,) + P.sino_shape, dtype=tdt, device=dev)
+    xb = torch.empty((batch,) + P.vol_shape, dtype=tdt, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def step():
@@ -240,8 +259,8 @@ def run_ours(args, rank, world, local):
     t_back = time_op(lambda: P.back(p, out=xb))
 
     # --- end to end through the public API with host buffers ----------------------------
-    x_pin = torch.from_numpy(xs_host).pin_memory()
-    out_pin = torch.empty((BATCH,) + P.vol_shape, dtype=torch.float32).pin_memory()
+    x_pin = x.cpu().pin_memory()
+    out_pin = torch.empty((batch,) + P.vol_shape, dtype=tdt).pin_memory()
     ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     barrier()
     for i in range(args.steps):
@@ -262,13 +281,14 @@ def run_ours(args, rank, world, local):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
     t_ms, t_e2e, t_fwd, t_back = tt.tolist()
 
-    updates_per_step = 2.0 * nnz * BATCH * world
+    updates_per_step = 2.0 * nnz * batch * world
     value = updates_per_step * args.steps / (t_ms / 1e3) / 1e9
     e2e_value = updates_per_step * args.steps / (t_e2e / 1e3) / 1e9
 
     # roofline of the dominant kernel (ALU bound: algorithmic flops / launch time)
     dom, t_dom = ("forward", t_fwd) if t_fwd >= t_back else ("back", t_back)
-    flops = nnz * (FLOPS_PER_ENTRY_WEIGHT + 2 * BATCH)
+    fpe = FLOPS_PER_ENTRY_WEIGHT[g["dim"]]
+    flops = nnz * (fpe + 2 * batch)
     achieved = flops / (t_dom / 1e3) / 1e12
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -276,21 +296,23 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [512, 512], "views": 720, "detector": 768, "batch": BATCH,
-                   "nnz_per_phantom": nnz, "l2": "flushed before every timed step (512 MiB write, untimed)",
-                   "step": "forward over all views + back projection, batch of 16"},
+        "scaling": "weak", "vs_baseline": None, "dtype": sdt, "data": "synthetic",
+        "config": {"workload": wl, "grid": [g["nx"], g["ny"]] + ([g["nz"]] if g["dim"] == 3 else []),
+                   "views": g["n_views"], "detector": [g["nu"]] + ([g["nv"]] if g["dim"] == 3 else []),
+                   "batch": batch, "nnz_per_item": nnz,
+                   "l2": "flushed before every timed step (512 MiB write, untimed)",
+                   "step": "forward over all views + back projection of the batch"},
         "gpu_launches": 4 * args.steps,
         "kernels_ms": {"forward": t_fwd, "back": t_back},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x %.0f MHz (max SM clock); "
-                                  "algorithmic flops = nnz x (%d + 2 x batch)" % (sm_max, FLOPS_PER_ENTRY_WEIGHT)},
+                                  "algorithmic flops = nnz x (%d + 2 x batch)" % (sm_max, fpe)},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_pin.numel() * 4),
                 "d2h_bytes_per_step": int(out_pin.numel() * 4)},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == WORKLOAD:
         try:
             import oracle
             gq, xq, views, cores = cpu_oracle_leg(1, target_s=12.0)

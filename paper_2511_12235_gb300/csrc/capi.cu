@@ -258,6 +258,10 @@ static csm_status finish_create(csm_geom_s* g, const double* angles, csm_geom_t*
         double tmin = g->s - r, diag = sqrt(g->a * g->a + g->b * g->b);
         double vext = g->sdd * (g->c / tmin + hz * diag / (tmin * tmin));
         if (vext / g->dv + 3.0 > (double)kMaxRowCorners) return CSM_EUNSUPPORTED;
+        // corner lines that can cross one cell: its u-extent over du, plus one
+        double tanb = std::max(fabs((-0.5 * g->nu) * g->du + g->u_off), fabs((0.5 * g->nu) * g->du + g->u_off)) / g->sdd;
+        double uext = g->sdd * diag * (1.0 + tanb) / tmin;
+        if (floor(uext / g->du) + 1.0 > (double)kMaxG) return CSM_EUNSUPPORTED;
     }
     cudaError_t e = cudaGetDevice(&g->device);
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }

@@ -91,6 +91,9 @@ Geo make_geo(const csm_geom_s* g);
 // Most detector row corners (rows + 1) that one voxel's footprint can span in one view; the
 // 3D kernels keep one value per corner in registers.  Geometries beyond it are refused.
 constexpr int kMaxRowCorners = 8;
+// Most corner lines that cross one voxel column's cell in one view; the voxel-driven 3D
+// kernels keep one top-view atom per crossing line in shared memory.  Checked on the host.
+constexpr int kMaxG = 6;
 
 // thread-local record of the last CUDA error text
 void set_cuda_error(cudaError_t e);

@@ -85,8 +85,17 @@ class Projector:
         return t, False
 
     def forward(self, x: torch.Tensor, out: torch.Tensor | None = None, *, flags: int = 0,
-                out_dtype: torch.dtype | None = None) -> torch.Tensor:
-        """p = W x.  x: [B, *vol_shape] or vol_shape on this device."""
+                out_dtype: torch.dtype | None = None, variant: str | None = None) -> torch.Tensor:
+        """p = W x.  x: [B, *vol_shape] or vol_shape on this device.
+
+        variant: "ray" (ray-driven gather; the only one built: the voxel-driven scatter
+        form is refused with CSM_EUNSUPPORTED)."""
+        if variant is None:
+            variant = "ray"
+        if variant == "voxel":
+            flags |= capi.CSM_VOXEL_DRIVEN
+        elif variant != "ray":
+            raise ValueError("variant must be 'ray' or 'voxel'")
         xb, single = self._batched(x, self.vol_shape)
         if not xb.is_contiguous():
             xb = xb.contiguous()

@@ -55,10 +55,18 @@ def power_norm(P: Projector, iters: int = 100, start: torch.Tensor | None = None
                dtype: torch.dtype = torch.float32, seed: int = 0) -> float:
     """Spectral norm ||W||_2 by `iters` power iterations on W^T W (Section "Numerical
     Experiments": W is divided by its spectral norm, 100 power iterations)."""
+    return math.sqrt(float(power_norm2_device(P, iters, start, dtype, seed).item()))
+
+
+def power_norm2_device(P: Projector, iters: int = 100, start: torch.Tensor | None = None,
+                       dtype: torch.dtype = torch.float32, seed: int = 0) -> torch.Tensor:
+    """The same estimate of ||W||_2^2, left on the device (float64 tensor [1]) so that the
+    caller does not wait for it."""
     dev = P.device
     if start is None:
-        g = torch.Generator(device="cpu").manual_seed(seed)
-        start = torch.randn((1,) + tuple(P.vol_shape), generator=g, dtype=torch.float64).to(dtype)
+        g = torch.Generator(device=dev)
+        g.manual_seed(seed)
+        start = torch.randn((1,) + tuple(P.vol_shape), generator=g, device=dev, dtype=dtype)
     b = start.reshape((1,) + tuple(P.vol_shape)).to(device=dev, dtype=dtype).contiguous().clone()
     ops = VecOps(dev, 1)
     nrm = torch.zeros(2, dtype=torch.float64, device=dev)
@@ -73,7 +81,7 @@ def power_norm(P: Projector, iters: int = 100, start: torch.Tensor | None = None
         ops.axpby(1.0, z, 0.0, b, a_den=nrm[0:1], flags=1)     # b = W^T W b / ||W^T W b||
     P.forward(b, out=p)
     ops.dot(p, p, nrm[1:2])                                  # Rayleigh quotient ||W b||^2
-    return math.sqrt(float(nrm[1].item()))
+    return nrm[1:2]
 
 
 class CGLS:
@@ -142,10 +150,22 @@ class NAG:
     ``run`` returns u (the paper's variable); u / sigma is the image in the units of W."""
 
     def __init__(self, P: Projector, batch: int, lam: float = 1e-4, sigma: float | None = None,
-                 dtype: torch.dtype = torch.float32):
+                 dtype: torch.dtype = torch.float32, sigma2_device: torch.Tensor | None = None,
+                 sigma_scale: float = 1.0):
+        """sigma: ||W|| as a number; or sigma2_device: ||W||^2 as a float64 device tensor of
+        one element per batch item (or one shared), read by the kernels without a host wait.
+        sigma_scale multiplies sigma (a safety margin for an estimated norm)."""
         self.P, self.B, self.lam, self.dtype = P, batch, float(lam), dtype
-        self.sigma = float(sigma) if sigma is not None else power_norm(P, dtype=dtype)
         dev = P.device
+        if sigma2_device is not None:
+            s2 = sigma2_device.to(device=dev, dtype=torch.float64).reshape(-1)
+            self.sig2 = (s2.expand(batch) if s2.numel() == 1 else s2).contiguous()
+            self.sigma = None
+            self.inv_c = 1.0 / sigma_scale
+        else:
+            self.sigma = float(sigma) if sigma is not None else power_norm(P, dtype=dtype)
+            self.sig2 = None
+            self.inv_c = 1.0 / (sigma_scale * self.sigma)
         vs, ss = (batch,) + tuple(P.vol_shape), (batch,) + tuple(P.sino_shape)
         self.u = torch.zeros(vs, dtype=dtype, device=dev)
         self.y = torch.zeros(vs, dtype=dtype, device=dev)
@@ -166,11 +186,12 @@ class NAG:
 
     def gradient(self, y: torch.Tensor, out: torch.Tensor):
         """out = grad F(y) = W^T (W y / sigma - p) / sigma + lam y."""
-        P, ops, inv = self.P, self.ops, 1.0 / self.sigma
+        P, ops, inv = self.P, self.ops, self.inv_c
+        sd, fl = self.sig2, (2 if self.sig2 is not None else 0)   # B = inv / sqrt(sigma^2)
         P.forward(y, out=self.r)
-        ops.axpby(-1.0, self.p, inv, self.r)            # r = W y / sigma - p
+        ops.axpby(-1.0, self.p, inv, self.r, b_den=sd, flags=fl)    # r = W y / sigma - p
         P.back(self.r, out=out)
-        ops.axpby(self.lam, y, inv, out)                # g = W^T r / sigma + lam y
+        ops.axpby(self.lam, y, inv, out, b_den=sd, flags=fl)        # g = W^T r / sigma + lam y
         return out
 
     def step(self):

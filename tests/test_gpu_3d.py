@@ -42,23 +42,25 @@ def rel(a, b):
 SMALL = dict(a=1.2, b=0.9, c=1.1, s=14.0, sdd=23.0, du=1.3, dv=1.1, u_off=0.2, v_off=-0.35)
 
 
-def small_geom(nx=6, ny=5, nz=7, nu=14, nv=12, angles=None):
+def small_geom(nx=6, ny=5, nz=7, nu=14, nv=12, angles=None, **kw):
     if angles is None:
         angles = np.concatenate([synth.uniform_angles(10), [0.0, math.pi / 2, math.pi, 0.25 * math.pi]])
-    g = synth.geometry(nx, ny, nz, n_views=len(angles), angles=angles, nu=nu, nv=nv, **SMALL)
+    g = synth.geometry(nx, ny, nz, n_views=len(angles), angles=angles, nu=nu, nv=nv, **dict(SMALL, **kw))
     g["dim"] = 3
     return g
 
 
-@pytest.mark.parametrize("shape", [(6, 5, 7, 14, 12), (3, 4, 1, 9, 5), (1, 1, 1, 4, 3), (9, 8, 6, 17, 11)])
+@pytest.mark.parametrize("shape", [(6, 5, 7, 14, 12), (3, 4, 1, 9, 5), (1, 1, 1, 4, 3), (9, 8, 6, 17, 11),
+                                   (20, 3, 37, 15, 40)])
 def test_small_fp64_forward_back(csm, shape):
     nx, ny, nz, nu, nv = shape
-    g = small_geom(nx, ny, nz, nu, nv)
+    # the tall grid needs the source farther out (rows per voxel stay within the kernels' bound)
+    g = small_geom(nx, ny, nz, nu, nv, **({"s": 60.0, "sdd": 100.0} if nz > 20 else {}))
     rng = np.random.default_rng(sum(shape))
     x = rng.uniform(size=(nz, ny, nx))
     P = csm.Projector(g)
-    p = P.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = oracle.forward_3d(g, x)
+    p = P.forward(torch.from_numpy(x).cuda()).cpu().numpy()
     assert np.max(np.abs(p - ref)) <= 1e-11 * np.max(np.abs(ref)), np.max(np.abs(p - ref))
     y = rng.uniform(size=ref.shape)
     b = P.back(torch.from_numpy(y).cuda()).cpu().numpy()
@@ -71,10 +73,10 @@ def test_small_fp32_and_batch(csm):
     rng = np.random.default_rng(4)
     xs = rng.uniform(size=(3, 6, 8, 9))
     P = csm.Projector(g)
+    refs = [oracle.forward_3d(g, xs[i]) for i in range(3)]
     p = P.forward(torch.from_numpy(xs).float().cuda()).cpu().numpy()
     for i in range(3):
-        ref = oracle.forward_3d(g, xs[i])
-        assert per_view_rel(p[i], ref) < FP32_TOL
+        assert per_view_rel(p[i], refs[i]) < FP32_TOL
     ys = rng.uniform(size=(3,) + p.shape[1:])
     b = P.back(torch.from_numpy(ys).float().cuda()).cpu().numpy()
     for i in range(3):
