@@ -115,6 +115,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def rank_seeds(rank: int, batch: int):
+    """Phantom seeds of one rank: every rank projects its own independent batch."""
+    return list(range(rank * batch, (rank + 1) * batch))
+
+
+def max_over_ranks(values, world: int, device="cpu"):
+    """Element-wise maximum of per-rank timings (the job finishes with its slowest rank)."""
+    import torch
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -203,7 +218,7 @@ def run_ours(args, rank, world, local):
     sdt = args.dtype or WORKLOADS[wl]["dtype"]
     tdt = {"f32": torch.float32, "f64": torch.float64, "bf16": torch.bfloat16, "f16": torch.float16}[sdt]
     g = synth.config(wl)
-    seeds = range(rank * batch, (rank + 1) * batch)
+    seeds = rank_seeds(rank, batch)
     if g["dim"] == 2:
         xs_host = np.stack([synth.ellipse_phantom(g["nx"], s) for s in seeds]).astype(np.float32)
     else:
@@ -274,12 +289,7 @@ def run_ours(args, rank, world, local):
     barrier()
     t_e2e = sum(a.elapsed_time(b) for a, b in ee)
 
-    # max over ranks
-    tt = torch.tensor([t_ms, t_e2e, t_fwd, t_back], dtype=torch.float64, device=dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-    t_ms, t_e2e, t_fwd, t_back = tt.tolist()
+    t_ms, t_e2e, t_fwd, t_back = max_over_ranks([t_ms, t_e2e, t_fwd, t_back], world, dev)
 
     updates_per_step = 2.0 * nnz * batch * world
     value = updates_per_step * args.steps / (t_ms / 1e3) / 1e9
