@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--requests", type=int, default=60, help="serving: number of requests")
+    ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate / measured capacity")
     ap.add_argument("--dtype", default=None, choices=["f32", "f64", "bf16", "f16"],
                     help="storage dtype of volume and sinogram (default per workload)")
     return ap.parse_args()
@@ -346,11 +348,81 @@ def run_ours(args, rank, world, local):
         dist.destroy_process_group()
 
 
+def run_serving(args, rank, world, local):
+    """Serving mix: Poisson arrivals of reconstruction requests (60% 2D, 40% 3D, 20 NAG
+    iterations each), served by the continuous-batching server against the same requests run
+    one at a time with plain calls.  Rank 0 only (one server per GPU)."""
+    import numpy as np
+    import torch
+    if rank != 0:
+        return
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import synth
+    import paper_2511_12235_gb300 as csm
+    from paper_2511_12235_gb300.serve import (ReconServer, Request, fifo_latencies, latency_stats,
+                                              solve_alone)
+    specs = synth.serving_requests(args.requests, seed=0, rate_per_s=1.0)
+    reqs = []
+    for sp in specs:      # measured data: projections of a seeded phantom with Poisson noise
+        g = sp["geom"]
+        P = csm.Projector(g, device=dev)
+        if g["dim"] == 2:
+            x = torch.from_numpy(synth.ellipse_phantom(g["nx"], sp["seed"])).float().to(dev)
+        else:
+            x = synth.ellipsoid_phantom_torch(g["nx"], sp["seed"], dev)
+        p = P.forward(x).double().cpu().numpy()
+        P.close()
+        pn, _ = synth.poisson_sinogram(p, seed=sp["seed"])
+        reqs.append(Request(id=sp["id"], geom=g, sino=pn.astype(np.float32), iters=20, power_iters=20,
+                            seed=sp["seed"]))
+    torch.cuda.synchronize()
+    # unbatched plain calls, one request at a time: the service time of each request
+    solve_alone(reqs[0], device=dev)          # warm-up
+    service = []
+    for r in reqs:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solve_alone(r, device=dev)
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t0)
+    cap = 1.0 / float(np.mean(service))
+    rate = args.load * cap
+    rng = np.random.default_rng(1)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    for r, a in zip(reqs, arrivals):
+        r.arrival = float(a)
+    base_lat = fifo_latencies(arrivals, service)
+    base_makespan = max(a + l for a, l in zip(arrivals, base_lat))
+    srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
+    t0 = time.perf_counter()
+    done = srv.serve(reqs, realtime=True)
+    makespan = time.perf_counter() - t0
+    lat = [r.latency for r in done]
+    st, bst = latency_stats(lat), latency_stats(base_lat)
+    line = {
+        "metric": METRIC, "value": len(done) / makespan, "unit": "requests/s", "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving", "requests": len(done), "share_2d": sum(r.geom["dim"] == 2 for r in done) / len(done),
+                   "nag_iterations": 20, "power_iterations": 20, "budget_gb": 120, "max_active": 16,
+                   "arrival_rate_per_s": rate, "load_vs_capacity": args.load},
+        "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+        "unbatched": {"requests_per_s": len(done) / base_makespan, "p50_s": bst["p50_s"], "p99_s": bst["p99_s"],
+                      "mean_service_s": float(np.mean(service)),
+                      "note": "same requests and arrivals, one at a time with plain csm_forward/csm_back calls "
+                              "(FIFO queue over the measured service times)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "serving":
+        run_serving(args, rank, world, local)
         return
     run_ours(args, rank, world, local)
 

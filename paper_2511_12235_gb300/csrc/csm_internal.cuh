@@ -157,6 +157,23 @@ __device__ __forceinline__ T relu_mean(T p, T q, T inv2) {
     return mx * mx * inv2;
 }
 
+// Branch-free form of the same atom (selects instead of branches): lanes of a warp that sit
+// in different cases issue the same instructions.  Exactly 1 when the line lies above the
+// cell and exactly 0 when it lies below.
+template <typename T>
+__device__ __forceinline__ T relu_mean_sel(T p, T q, T inv2) {
+    const T mx = p > q ? p : q, mn = p > q ? q : p;
+    const T r = mx > T(0) ? mx : T(0);
+    return mn >= T(0) ? T(0.5) * (p + q) : r * r * inv2;
+}
+
+template <typename T>
+__device__ __forceinline__ T cell_atom(T p, T q, T inv2) {
+    const T mn = p > q ? q : p;
+    const T v = relu_mean_sel(p, q, inv2) - relu_mean_sel(p - T(1), q - T(1), inv2);
+    return mn >= T(1) ? T(1) : v;
+}
+
 template <typename T>
 __device__ __forceinline__ T cell_below(T p, T q, T inv2) {
     T mx = p > q ? p : q;

@@ -115,24 +115,46 @@ __global__ void prep_sino_2d(const void* __restrict__ p, int pdt, int B, int b_o
 
 // acc[b] += wt * value[b] for the NB items of one cell; `base` points at the cell's first
 // vector and consecutive planes are `plane` elements apart.
-template <typename T, int NB>
-__device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict__ base, size_t plane) {
-    constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
-    if constexpr (sizeof(T) == 4 && VW == 4) {
+template <typename T, int NB> struct Cell;   // the NB values of one cell, in registers
+template <int NB> struct Cell<float, NB> {
+    static constexpr int Q = Vec<NB>::Q;
+    float4 v[Q];
+    __device__ __forceinline__ void load(const float* __restrict__ base, size_t plane) {
+        if constexpr (Vec<NB>::W == 4) {
 #pragma unroll
-        for (int q = 0; q < Q; ++q) {
-            float4 v = __ldg(reinterpret_cast<const float4*>(base + q * plane));
-            acc[4 * q + 0] += wt * v.x;
-            acc[4 * q + 1] += wt * v.y;
-            acc[4 * q + 2] += wt * v.z;
-            acc[4 * q + 3] += wt * v.w;
+            for (int q = 0; q < Q; ++q) v[q] = __ldg(reinterpret_cast<const float4*>(base + q * plane));
+        } else {
+#pragma unroll
+            for (int r = 0; r < NB; ++r) (&v[0].x)[r] = __ldg(base + r);
         }
-    } else {
+    }
+    __device__ __forceinline__ void fma(float (&acc)[NB], float wt) const {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc[i] += wt * (&v[0].x)[i];
+    }
+};
+template <int NB> struct Cell<double, NB> {
+    static constexpr int Q = Vec<NB>::Q, W = Vec<NB>::W;
+    double v[NB];
+    __device__ __forceinline__ void load(const double* __restrict__ base, size_t plane) {
 #pragma unroll
         for (int q = 0; q < Q; ++q)
 #pragma unroll
-            for (int r = 0; r < VW; ++r) acc[q * VW + r] += wt * __ldg(base + q * plane + r);
+            for (int r = 0; r < W; ++r) v[q * W + r] = __ldg(base + q * plane + r);
     }
+    __device__ __forceinline__ void fma(double (&acc)[NB], double wt) const {
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc[i] += wt * v[i];
+    }
+};
+
+// acc[b] += wt * value[b] for the NB items of one cell; `base` points at the cell's first
+// vector and consecutive planes are `plane` elements apart.
+template <typename T, int NB>
+__device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict__ base, size_t plane) {
+    Cell<T, NB> cell;
+    cell.load(base, plane);
+    cell.fma(acc, wt);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -162,15 +184,27 @@ __global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0
     for (int w = w0; w < w1; ++w) {
         int clo = min(la.cell_lo(), lb.cell_lo());
         int chi = max(la.cell_hi(), lb.cell_hi());
-        clo = max(clo, 0);
+        const int c0 = max(clo, 0);
         chi = min(chi, nc - 1);
-        for (int c = clo; c <= chi; ++c) {
+        if (c0 <= chi) {
+            // both lines' cross offsets at the two walk faces, relative to cell c0, converted
+            // once per column; per cell only an integer shift remains
             T a0, a1, b0, b1;
-            la.offsets(c, a0, a1);
-            lb.offsets(c, b0, b1);
-            const T fa = cell_below(a0, a1, ia), fb = cell_below(b0, b1, ib);
-            const T wt = sigma > 0 ? fb - fa : fa - fb;
-            if (wt != T(0)) fma_cell<T, NB>(acc, wt, xs + ((size_t)w * Vec<NB>::Q * nc + c) * Vec<NB>::W, (size_t)nc * Vec<NB>::W);
+            la.offsets(c0, a0, a1);
+            lb.offsets(c0, b0, b1);
+            const T* xw = xs + ((size_t)w * Vec<NB>::Q * nc) * Vec<NB>::W;
+            for (int c = c0; c <= chi; ++c) {
+                // the cell's values first: their latency overlaps the weight arithmetic
+                Cell<T, NB> cell;
+                cell.load(xw + (size_t)c * Vec<NB>::W, (size_t)nc * Vec<NB>::W);
+                const T fa = cell_atom(a0, a1, ia), fb = cell_atom(b0, b1, ib);
+                const T wt = sigma > 0 ? fb - fa : fa - fb;
+                cell.fma(acc, wt);
+                a0 -= T(1);
+                a1 -= T(1);
+                b0 -= T(1);
+                b1 -= T(1);
+            }
         }
         la.step();
         lb.step();
@@ -275,15 +309,17 @@ __global__ void __launch_bounds__(BTX * BTY * BG) back2d_vox(Geo g, const T* __r
             l.load(g, v, k0, w);
             T y0, y1;
             l.offsets(c, y0, y1);
-            T prev = cell_below(y0, y1, inv_of<T>(g, v, k0));
+            T prev = cell_atom(y0, y1, inv_of<T>(g, v, k0));
             const T* pv = ps + (size_t)v * Q * plane;
             for (int k = k0; k <= k1; ++k) {
+                Cell<T, NB> cell;
+                cell.load(pv + (size_t)k * VW, plane);   // issued before the weight arithmetic
                 l.load(g, v, k + 1, w);
                 l.offsets(c, y0, y1);
-                const T cur = cell_below(y0, y1, inv_of<T>(g, v, k + 1));
+                const T cur = cell_atom(y0, y1, inv_of<T>(g, v, k + 1));
                 const T wt = sigma > 0 ? cur - prev : prev - cur;
                 prev = cur;
-                if (wt != T(0)) fma_cell<T, NB>(acc, wt, pv + (size_t)k * VW, plane);
+                cell.fma(acc, wt);
             }
         }
     }

@@ -156,6 +156,31 @@ def ellipsoid_phantom(n: int, seed: int, n_ellipsoids: int = 10, dtype=np.float6
     return out
 
 
+def ellipsoid_phantom_torch(n: int, seed: int, device, n_ellipsoids: int = 10):
+    """The same phantom as ``ellipsoid_phantom`` (same parameter draws), evaluated with torch
+    on ``device`` (float32), for large serving requests."""
+    import torch
+    rng = np.random.default_rng(seed)
+    R = 0.5 * n
+    xs = torch.arange(n, device=device, dtype=torch.float32) - n / 2.0 + 0.5
+    Z, Y, X = torch.meshgrid(xs, xs, xs, indexing="ij")
+    out = torch.zeros((n, n, n), device=device, dtype=torch.float32)
+    for _ in range(n_ellipsoids):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        c = d * 0.7 * R * rng.uniform() ** (1.0 / 3.0)
+        ax = rng.uniform(0.05, 0.35, size=3) * R
+        Rm = _random_rotation(rng)
+        val = rng.uniform(0, 1)
+        dx, dy, dz = X - float(c[0]), Y - float(c[1]), Z - float(c[2])
+        q = torch.zeros_like(out)
+        for r in range(3):
+            comp = float(Rm[0, r]) * dx + float(Rm[1, r]) * dy + float(Rm[2, r]) * dz
+            q += (comp / float(ax[r])) ** 2
+        out += (q <= 1.0).float() * float(val)
+    return out
+
+
 def poisson_sinogram(p: np.ndarray, seed: int, photons: float = 1e5, max_line: float = 3.0):
     """Poisson noise at ``photons`` incident counts.
 
