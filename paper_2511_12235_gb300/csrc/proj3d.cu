@@ -261,18 +261,25 @@ __device__ __forceinline__ T tail_moment(const AtomE<T>& P, T Tq, T s) {
     return -s * acc * T(1.0 / 6.0);
 }
 
-// Phi = integral over the atom of clamp(g + q t', 0, c); iq = 1 / |q|.
+// Phi = integral over the atom of clamp(g + q t', 0, c); iq = 1 / |q|.  In the flipped frame
+// s t' the clamp's kinks sit at T0 = -g/|q| (bottom face) and T1 = (c - g)/|q| (top face);
+// only a kink inside the atom's depth range needs the edge sum, and normally only one is
+// inside, so one tail evaluation serves both terms (a second one only for voxels thinner
+// than the plane's rise across the atom).
 template <typename T>
 __device__ __forceinline__ T phi_e(const AtomE<T>& P, T g, T q, T iq, T c) {
     if (q == T(0)) return (g < T(0) ? T(0) : (g > c ? c : g)) * P.A;
     const T s = q > T(0) ? T(1) : T(-1), qa = fabs(q);
     const T T0 = -g * iq, T1 = (c - g) * iq;
     const T lo = s > T(0) ? P.tmin : -P.tmax, hi = s > T(0) ? P.tmax : -P.tmin;
-    if (T1 <= lo) return c * P.A;           // plane above the top face over the whole atom
-    if (T0 >= hi) return T(0);              // plane below the bottom face over the whole atom
-    const T M1s = s * P.M1;
-    const T P0 = T0 <= lo ? g * P.A + qa * M1s : qa * tail_moment(P, T0, s);
-    const T P1 = T1 >= hi ? T(0) : qa * tail_moment(P, T1, s);
+    const T lin0 = g * P.A + qa * s * P.M1;        // q |q| M(T0) when T0 <= lo
+    const T lin1 = lin0 - c * P.A;                 // q |q| M(T1) when T1 <= lo
+    const bool in0 = T0 > lo && T0 < hi, in1 = T1 > lo && T1 < hi;
+    if (!in0 && !in1) return T1 <= lo ? c * P.A : (T0 >= hi ? T(0) : lin0);
+    const T tl = qa * tail_moment(P, in0 ? T0 : T1, s);
+    const T P0 = in0 ? tl : (T0 <= lo ? lin0 : T(0));
+    T P1 = in1 ? tl : (T1 >= hi ? T(0) : lin1);
+    if (in0 && in1) P1 = qa * tail_moment(P, T1, s);
     return P0 - P1;
 }
 
@@ -384,59 +391,52 @@ __device__ __forceinline__ bool voxel_rows(const Geo& g, T z0w, T z1w, T tmin, T
 }
 
 // Visits every nonzero W(k, l) of voxel iz in the column (ix, iy) for view v:
-// emit(k, l, W).  atoms: the column-view's crossing-line atoms; full: the whole-cell atom.
+// emit(k, l, W).  atoms: the column-view's crossing-line atoms; full: the whole-cell atom;
+// scratch: this lane's 2 (kMaxG + 1) slots, 32 elements apart (one per lane of the warp), for
+// Phi per atom on two consecutive row corner planes.
 template <typename T, typename Emit>
 __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int iy, int iz, const ColumnView<T>& cv,
-                                              const AtomE<T>* atoms, const AtomE<T>& full, Emit&& emit) {
+                                              const AtomE<T>* atoms, const AtomE<T>& full, T* scratch, Emit&& emit) {
     using R = typename RowOf<T>::type;
     const T c = G3<T>::c(g);
     const T z0w = G3<T>::z0(g) + iz * c;
     int l0, l1;
     if (!voxel_rows<T>(g, z0w, z0w + c, cv.tmin_w, cv.tmax_w, l0, l1)) return;
-    T pf = T(0), pg[kMaxG];
-#pragma unroll
-    for (int i = 0; i < kMaxG; ++i) pg[i] = T(0);
-    const int ng = cv.ng;
+    const int ng = cv.ng, na = ng + 1;
+    // PHI(b, j): Phi of atom j (0: the whole cell, j > 0: crossing line j - 1) on the row
+    // corner plane held in buffer b; buffers alternate between the corners r - 1 and r
+#define PHI(b, j) scratch[((b) * (kMaxG + 1) + (j)) * 32]
+#pragma unroll 1
     for (int r = l0; r <= l1 + 1; ++r) {
+        const int cur = r & 1, prv = cur ^ 1;
         R row;
         row.at(g, v, r, ix, iy);
         const T h = row.rel(iz);                 // plane height above the voxel bottom, units of c
         const T q = G3<T>::q(g, r);
         const T m = fabs(q) * cv.margin / c;     // height change across the cell, units of c
-        T cf, cgv[kMaxG];
-        if (h + m <= T(0)) {                     // plane below the voxel everywhere in the cell
-            cf = T(0);
-#pragma unroll
-            for (int i = 0; i < kMaxG; ++i) cgv[i] = T(0);
-        } else if (h - m >= T(1)) {              // plane above the voxel everywhere
-            cf = c * full.A;
-#pragma unroll
-            for (int i = 0; i < kMaxG; ++i) cgv[i] = i < ng ? c * atoms[i].A : T(0);
-        } else {
-            const T gw = h * c, iq = q != T(0) ? G3<T>::div(T(1), fabs(q)) : T(0);
-            cf = phi_e<T>(full, gw, q, iq, c);
-#pragma unroll
-            for (int i = 0; i < kMaxG; ++i) cgv[i] = i < ng ? phi_e<T>(atoms[i], gw, q, iq, c) : T(0);
+        const int cls = h + m <= T(0) ? 0 : (h - m >= T(1) ? 2 : 1);   // below / above / crossing
+        const T gw = h * c, iq = q != T(0) ? G3<T>::div(T(1), fabs(q)) : T(0);
+#pragma unroll 1
+        for (int j = 0; j < na; ++j) {
+            const AtomE<T>& P = j == 0 ? full : atoms[j - 1];
+            PHI(cur, j) = cls == 0 ? T(0) : (cls == 2 ? c * P.A : phi_e<T>(P, gw, q, iq, c));
         }
-        if (r > l0) {
-            const int l = r - 1;
-            const T sf = cf - pf;
-            T prevS = cv.sigma > 0 ? T(0) : sf;  // S of the line before the first crossing line
-#pragma unroll
-            for (int j = 0; j <= kMaxG; ++j) {
-                if (j <= ng) {
-                    const T S = j < ng ? cgv[j] - pg[j] : (cv.sigma > 0 ? sf : T(0));
-                    const int k = cv.k_first + j;
-                    const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
-                    if (k >= 0 && k < g.nu && wt != T(0)) emit(k, l, wt);
-                    prevS = S;
-                }
-            }
+        if (r == l0) continue;
+        // W(k, l) = sigma [S(k+1) - S(k)] with S = 0 (empty lines), S_full (whole-cell lines)
+        // or the crossing lines' S, over the element columns k_first .. k_first + ng
+        const int l = r - 1;
+        const T sf = PHI(cur, 0) - PHI(prv, 0);
+        T prevS = cv.sigma > 0 ? T(0) : sf;
+#pragma unroll 1
+        for (int j = 0; j <= ng; ++j) {
+            const T S = j < ng ? PHI(cur, j + 1) - PHI(prv, j + 1) : (cv.sigma > 0 ? sf : T(0));
+            const int k = cv.k_first + j;
+            const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
+            if (k >= 0 && k < g.nu && wt != T(0)) emit(k, l, wt);
+            prevS = S;
         }
-        pf = cf;
-#pragma unroll
-        for (int i = 0; i < kMaxG; ++i) pg[i] = cgv[i];
     }
+#undef PHI
 }
 
 // ---------------------------------------------------------------------------------------
@@ -452,6 +452,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
                                                       int B, int b_off, T scale, int accumulate) {
     __shared__ AtomE<T> atoms_s[BW][kMaxG + 1];
+    __shared__ T scratch_s[BW][2 * (kMaxG + 1) * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;                       // whole warp leaves together
@@ -459,6 +460,7 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
     const int iz = blockIdx.y * 32 + lane;
     AtomE<T>* atoms = atoms_s[wid];
     AtomE<T>& full = atoms_s[wid][kMaxG];
+    T* scratch = scratch_s[wid] + lane;
     T acc[NB];
 #pragma unroll
     for (int i = 0; i < NB; ++i) acc[i] = T(0);
@@ -472,7 +474,7 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
         __syncwarp();
         if (iz < g.nz) {
             const T* pv = ps + (size_t)v * g.nv * g.nu * NB;
-            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, full, [&](int k, int l, T wt) {
+            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, full, scratch, [&](int k, int l, T wt) {
                 fma_vec<T, NB>(acc, wt, pv + ((size_t)l * g.nu + k) * NB);
             });
         }
@@ -637,6 +639,7 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
 // in the back projection).
 __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long long* counter) {
     __shared__ AtomE<float> atoms_s[BW][kMaxG + 1];
+    __shared__ float scratch_s[BW][2 * (kMaxG + 1) * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;
@@ -644,6 +647,7 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
     const int iz = blockIdx.y * 32 + lane;
     AtomE<float>* atoms = atoms_s[wid];
     AtomE<float>& full = atoms_s[wid][kMaxG];
+    float* scratch = scratch_s[wid] + lane;
     const float thr = 1e-6f * g.a * g.b * g.c;
     unsigned long long cnt = 0;
     for (int v = 0; v < g.n_views; ++v) {
@@ -655,7 +659,8 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
         if (lane == 31) full_atom<float>(g, v, full);
         __syncwarp();
         if (iz < g.nz)
-            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, full, [&](int, int, float wt) { cnt += fabsf(wt) > thr; });
+            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, full, scratch,
+                                 [&](int, int, float wt) { cnt += fabsf(wt) > thr; });
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if (lane == 0 && cnt) atomicAdd(counter, cnt);
