@@ -72,6 +72,9 @@ struct Geo {
     // grid and detector in float and double
     float a, b, c, s, sdd, du, dv, u0, v0, x0, y0, z0;
     double a_d, b_d, c_d, s_d, sdd_d, du_d, dv_d, u0_d, v0_d, x0_d, y0_d, z0_d;
+    // reciprocals 1/du, 1/dv, 1/c (rounded from FP64), so that no kernel divides by them
+    float idu, idv, ic;
+    double idu_d, idv_d, ic_d;
     const int* axis_sigma;
     const float* cs_f;
     const double* cs_d;

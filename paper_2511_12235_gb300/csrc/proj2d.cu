@@ -226,6 +226,7 @@ template <> struct GeoT<float> {
     static __device__ __forceinline__ float sdd(const Geo& g) { return g.sdd; }
     static __device__ __forceinline__ float u0(const Geo& g) { return g.u0; }
     static __device__ __forceinline__ float du(const Geo& g) { return g.du; }
+    static __device__ __forceinline__ float idu(const Geo& g) { return g.idu; }
     static __device__ __forceinline__ float x0(const Geo& g) { return g.x0; }
     static __device__ __forceinline__ float y0(const Geo& g) { return g.y0; }
     static __device__ __forceinline__ float a(const Geo& g) { return g.a; }
@@ -236,6 +237,7 @@ template <> struct GeoT<double> {
     static __device__ __forceinline__ double sdd(const Geo& g) { return g.sdd_d; }
     static __device__ __forceinline__ double u0(const Geo& g) { return g.u0_d; }
     static __device__ __forceinline__ double du(const Geo& g) { return g.du_d; }
+    static __device__ __forceinline__ double idu(const Geo& g) { return g.idu_d; }
     static __device__ __forceinline__ double x0(const Geo& g) { return g.x0_d; }
     static __device__ __forceinline__ double y0(const Geo& g) { return g.y0_d; }
     static __device__ __forceinline__ double a(const Geo& g) { return g.a_d; }
@@ -265,7 +267,7 @@ __device__ __forceinline__ bool pixel_elements(const Geo& g, int v, T X0, T X1, 
         umin = u < umin ? u : umin;
         umax = u > umax ? u : umax;
     }
-    const T inv_du = T(1) / GeoT<T>::du(g);
+    const T inv_du = GeoT<T>::idu(g);
     T f0 = floor((umin - GeoT<T>::u0(g)) * inv_du - RangeEps<T>::v);
     T f1 = floor((umax - GeoT<T>::u0(g)) * inv_du + RangeEps<T>::v);
     f0 = f0 < T(-2) ? T(-2) : (f0 > T(g.nu + 2) ? T(g.nu + 2) : f0);

@@ -94,6 +94,9 @@ template <> struct G3<float> {
     static __device__ __forceinline__ float v0(const Geo& g) { return g.v0; }
     static __device__ __forceinline__ float du(const Geo& g) { return g.du; }
     static __device__ __forceinline__ float dv(const Geo& g) { return g.dv; }
+    static __device__ __forceinline__ float idu(const Geo& g) { return g.idu; }
+    static __device__ __forceinline__ float idv(const Geo& g) { return g.idv; }
+    static __device__ __forceinline__ float ic(const Geo& g) { return g.ic; }
     static __device__ __forceinline__ float cs(const Geo& g, int v, int i) { return g.cs_f[2 * v + i]; }
     static __device__ __forceinline__ float q(const Geo& g, int l) { return g.rowq_f[l]; }
     static __device__ __forceinline__ float div(float x, float y) { return __fdividef(x, y); }
@@ -112,6 +115,9 @@ template <> struct G3<double> {
     static __device__ __forceinline__ double v0(const Geo& g) { return g.v0_d; }
     static __device__ __forceinline__ double du(const Geo& g) { return g.du_d; }
     static __device__ __forceinline__ double dv(const Geo& g) { return g.dv_d; }
+    static __device__ __forceinline__ double idu(const Geo& g) { return g.idu_d; }
+    static __device__ __forceinline__ double idv(const Geo& g) { return g.idv_d; }
+    static __device__ __forceinline__ double ic(const Geo& g) { return g.ic_d; }
     static __device__ __forceinline__ double cs(const Geo& g, int v, int i) { return g.cs_d[2 * v + i]; }
     static __device__ __forceinline__ double q(const Geo& g, int l) { return g.rowq_d[l]; }
     static __device__ __forceinline__ double div(double x, double y) { return x / y; }
@@ -183,27 +189,56 @@ __device__ __forceinline__ void fma_vec(T (&acc)[NB], T wt, const T* __restrict_
 }
 
 // ---------------------------------------------------------------------------------------
-// Edge form of a top-view atom for repeated evaluation.  Per edge: the depths t' of its two
-// ends, w_e = e_s . (outward normal x length) and 1 / |t'_a - t'_b|; zero-length edges are
-// dropped.  The tail moment
-//     M_s(T) = integral over the atom of relu(s t' - T) dA   (s = +1 or -1)
-// is  -(s/6) sum_e w_e E_e  with E_e = a^2 + a b + b^2 (both ends beyond T) or
-// a^3 / |t'_a - t'_b| (one end beyond T), a >= b the parts of the ends beyond T: the same
-// edge sum as above with the per-edge division precomputed.
+// Tail-moment table of a top-view atom.  The tail moment
+//     M(T) = integral over the atom of relu(t' - T) dA
+// (t' = depth relative to the cell centre) is a cubic in T between consecutive vertex depths
+// of the atom: by the divergence theorem it is  -(1/6) sum_e w_e E_e(T)  over the atom's
+// edges, w_e = e_s . (outward normal x length) projected on the source direction and
+// E_e = a^2 + a b + b^2 (both ends beyond T) or a^3 / |t'_a - t'_b| (one end beyond T),
+// a >= b the parts of the ends beyond T.  These are the paper's cubic terms C g^3
+// (Eq. (rel vol 3d), Eq. (res vol 3d)) written per edge instead of per vertex, which removes
+// the 1/sin(phi), 1/cos(phi) factors of the printed forms (their singular views, Eq. (vol))
+// from the arithmetic.  The table holds the six vertex depths sorted, tau_0 <= .. <= tau_5,
+// and per piece the Taylor coefficients of M at the piece's base:
+//     piece 0      T <  tau_0                linear  M(tau_0) - A (T - tau_0)
+//     piece p      tau_{p-1} <= T < tau_p    cubic, base tau_{p-1}   (p = 1 .. 5)
+//     piece 6      T >= tau_5                zero
+// so that M costs six comparisons and three FMAs, the same for every lane.
 // ---------------------------------------------------------------------------------------
 
 template <typename T>
 __device__ __forceinline__ T clamp01(T v) { return v < T(0) ? T(0) : (v > T(1) ? T(1) : v); }
 
 template <typename T>
-struct AtomE {
-    T ta[6], tb[6], w[6], inv[6];
-    T A, M1, tmin, tmax;
-    int ne;
+struct __align__(16) AtomP {
+    T cf[7][4];   // per piece: M and its first three derivatives / n! at the piece's base
+    T tau[6];     // sorted vertex depths
+    T A;          // area
+    T pad;
 };
 
+template <typename T> struct Cf4;
+template <> struct Cf4<float> {
+    float x, y, z, w;
+    __device__ __forceinline__ void load(const float* p) {
+        const float4 v = *reinterpret_cast<const float4*>(p);
+        x = v.x; y = v.y; z = v.z; w = v.w;
+    }
+};
+template <> struct Cf4<double> {
+    double x, y, z, w;
+    __device__ __forceinline__ void load(const double* p) {
+        const double2 v0 = reinterpret_cast<const double2*>(p)[0], v1 = reinterpret_cast<const double2*>(p)[1];
+        x = v0.x; y = v0.y; z = v1.x; w = v1.y;
+    }
+};
+
+// Piece p (1 <= p <= 5) of the table of the atom "cell below the line with offsets lam0, lam1
+// at the walk boundaries" (units of hc; lam >= 1 on both ends: the whole cell); the call with
+// p == 1 also writes tau, A and pieces 0 and 6.  Every lane that builds a piece of the same
+// atom computes the same vertices and the same sorted depths.
 template <typename T>
-__device__ __forceinline__ void make_atom_e(AtomE<T>& P, T lam0, T lam1, T hw, T hc, int axis, T cs, T sn) {
+__device__ __forceinline__ void build_piece(AtomP<T>& P, int p, T lam0, T lam1, T hw, T hc, int axis, T cs, T sn) {
     const T dl = lam1 - lam0;
     T xa = T(1), xb = T(1);
     if (dl != T(0)) {
@@ -212,6 +247,7 @@ __device__ __forceinline__ void make_atom_e(AtomE<T>& P, T lam0, T lam1, T hw, T
         xb = clamp01((T(1) - lam0) * r);
     }
     const T xhi = xa > xb ? xa : xb, xlo = xa > xb ? xb : xa;
+    // vertices in cell units (walk coordinate XI, cross coordinate ET), counter-clockwise
     const T XI[6] = {T(0), T(1), T(1), xhi, xlo, T(0)};
     const T ET[6] = {T(0), T(0), clamp01(lam1), clamp01(lam0 + dl * xhi), clamp01(lam0 + dl * xlo), clamp01(lam0)};
     T DX[6], DY[6], TP[6];
@@ -222,65 +258,83 @@ __device__ __forceinline__ void make_atom_e(AtomE<T>& P, T lam0, T lam1, T hw, T
         DY[i] = axis == 0 ? dc : dw;
         TP[i] = -(DX[i] * cs + DY[i] * sn);
     }
+    T ts[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) ts[i] = TP[i];
+    // sorting network for six keys
+#define CSM_CX(i, j) { const T lo_ = ts[i] < ts[j] ? ts[i] : ts[j], hi_ = ts[i] < ts[j] ? ts[j] : ts[i]; ts[i] = lo_; ts[j] = hi_; }
+    CSM_CX(0, 5) CSM_CX(1, 3) CSM_CX(2, 4) CSM_CX(1, 2) CSM_CX(3, 4) CSM_CX(0, 3)
+    CSM_CX(2, 5) CSM_CX(0, 1) CSM_CX(2, 3) CSM_CX(4, 5) CSM_CX(1, 2) CSM_CX(3, 4)
+#undef CSM_CX
+    T base = ts[0], top = ts[1];
+#pragma unroll
+    for (int i = 1; i < 5; ++i)
+        if (p == i + 1) { base = ts[i]; top = ts[i + 1]; }
+    const T mid = T(0.5) * (base + top);
     const T orient = axis == 0 ? T(1) : T(-1);
-    T a2 = T(0), m = T(0), tmin = TP[0], tmax = TP[0];
-    int ne = 0;
+    T c0 = T(0), c1 = T(0), c2 = T(0), c3 = T(0);
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const int j = (i + 1) % 6;
-        a2 += XI[i] * ET[j] - XI[j] * ET[i];
-        tmin = TP[i] < tmin ? TP[i] : tmin;
-        tmax = TP[i] > tmax ? TP[i] : tmax;
-        if (XI[i] == XI[j] && ET[i] == ET[j]) continue;
         const T w = orient * (cs * (DY[j] - DY[i]) - sn * (DX[j] - DX[i]));
-        const T d = fabs(TP[i] - TP[j]);
-        m -= w * (TP[i] * TP[i] + TP[i] * TP[j] + TP[j] * TP[j]);
-        P.ta[ne] = TP[i];
-        P.tb[ne] = TP[j];
-        P.w[ne] = w;
-        P.inv[ne] = d > T(0) ? G3<T>::div(T(1), d) : T(0);
-        ++ne;
+        const T hi = TP[i] > TP[j] ? TP[i] : TP[j], lo = TP[i] > TP[j] ? TP[j] : TP[i];
+        const T a = hi - base, b = lo - base;
+        if (mid < lo) {                 // both ends beyond T on the whole piece
+            c0 += w * (a * a + a * b + b * b);
+            c1 -= w * T(3) * (a + b);
+            c2 += w * T(3);
+        } else if (mid < hi) {          // one end beyond
+            const T inv = G3<T>::div(T(1), hi - lo);
+            c0 += w * a * a * a * inv;
+            c1 -= w * T(3) * a * a * inv;
+            c2 += w * T(3) * a * inv;
+            c3 -= w * inv;
+        }
     }
-    P.ne = ne;
-    P.A = T(0.5) * a2 * hw * hc;
-    P.M1 = m * T(1.0 / 6.0);
-    P.tmin = tmin;
-    P.tmax = tmax;
+    const T k = T(-1.0 / 6.0);
+    T* row = P.cf[p];
+    row[0] = k * c0; row[1] = k * c1; row[2] = k * c2; row[3] = k * c3;
+    if (p == 1) {
+        P.cf[0][0] = k * c0; P.cf[0][1] = k * c1; P.cf[0][2] = T(0); P.cf[0][3] = T(0);
+        P.cf[6][0] = T(0); P.cf[6][1] = T(0); P.cf[6][2] = T(0); P.cf[6][3] = T(0);
+        T a2 = T(0);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const int j = (i + 1) % 6;
+            a2 += XI[i] * ET[j] - XI[j] * ET[i];
+            P.tau[i] = ts[i];
+        }
+        P.A = T(0.5) * a2 * hw * hc;
+    }
 }
 
+// M(x) from the table; tau: the table's sorted depths, already in registers.
 template <typename T>
-__device__ __forceinline__ T tail_moment(const AtomE<T>& P, T Tq, T s) {
-    T acc = T(0);
-    for (int e = 0; e < P.ne; ++e) {
-        const T pa = s * P.ta[e] - Tq, pb = s * P.tb[e] - Tq;
-        const T mx = pa > pb ? pa : pb, mn = pa > pb ? pb : pa;
-        const T a = mx > T(0) ? mx : T(0), b = mn > T(0) ? mn : T(0);
-        const T E = b > T(0) ? (a * a + a * b + b * b) : a * a * a * P.inv[e];
-        acc += P.w[e] * E;
-    }
-    return -s * acc * T(1.0 / 6.0);
+__device__ __forceinline__ T eval_m(const AtomP<T>& P, const T (&tau)[6], T x) {
+    int idx = 0;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) idx += x >= tau[i] ? 1 : 0;
+    const T base = P.tau[idx > 0 ? idx - 1 : 0];
+    Cf4<T> c;
+    c.load(P.cf[idx]);
+    const T d = x - base;
+    return ((c.w * d + c.z) * d + c.y) * d + c.x;
 }
 
-// Phi = integral over the atom of clamp(g + q t', 0, c); iq = 1 / |q|.  In the flipped frame
-// s t' the clamp's kinks sit at T0 = -g/|q| (bottom face) and T1 = (c - g)/|q| (top face);
-// only a kink inside the atom's depth range needs the edge sum, and normally only one is
-// inside, so one tail evaluation serves both terms (a second one only for voxels thinner
-// than the plane's rise across the atom).
+// Phi = integral over the atom of clamp(g + q t', 0, c) dA, iq = 1 / |q| (0 for q = 0).
+// The clamp is relu(g + q t') - relu(g + q t' - c), whose kinks are the plane's crossings of
+// the voxel's bottom and top faces; for q > 0 the two relu integrals are |q| M(-g/|q|) and
+// |q| M((c - g)/|q|), for q < 0 the mirror relu(-y) = relu(y) - y gives
+// |q| [M(g/|q|) - M((g - c)/|q|)] + c A.
 template <typename T>
-__device__ __forceinline__ T phi_e(const AtomE<T>& P, T g, T q, T iq, T c) {
-    if (q == T(0)) return (g < T(0) ? T(0) : (g > c ? c : g)) * P.A;
-    const T s = q > T(0) ? T(1) : T(-1), qa = fabs(q);
-    const T T0 = -g * iq, T1 = (c - g) * iq;
-    const T lo = s > T(0) ? P.tmin : -P.tmax, hi = s > T(0) ? P.tmax : -P.tmin;
-    const T lin0 = g * P.A + qa * s * P.M1;        // q |q| M(T0) when T0 <= lo
-    const T lin1 = lin0 - c * P.A;                 // q |q| M(T1) when T1 <= lo
-    const bool in0 = T0 > lo && T0 < hi, in1 = T1 > lo && T1 < hi;
-    if (!in0 && !in1) return T1 <= lo ? c * P.A : (T0 >= hi ? T(0) : lin0);
-    const T tl = qa * tail_moment(P, in0 ? T0 : T1, s);
-    const T P0 = in0 ? tl : (T0 <= lo ? lin0 : T(0));
-    T P1 = in1 ? tl : (T1 >= hi ? T(0) : lin1);
-    if (in0 && in1) P1 = qa * tail_moment(P, T1, s);
-    return P0 - P1;
+__device__ __forceinline__ T phi_p(const AtomP<T>& P, T g, T q, T iq, T c) {
+    const T qa = fabs(q), sg = q < T(0) ? T(-1) : T(1);
+    const T x0 = -g * iq * sg, x1 = (c - g) * iq * sg;
+    T tau[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) tau[i] = P.tau[i];
+    const T r = qa * (eval_m<T>(P, tau, x0) - eval_m<T>(P, tau, x1)) + (q < T(0) ? c * P.A : T(0));
+    return q == T(0) ? (g < T(0) ? T(0) : (g > c ? c : g)) * P.A : r;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -296,34 +350,40 @@ template <typename T>
 struct ColumnView {
     int ok, axis, sigma, k_first, ng;   // elements k_first .. k_first + ng (ng + 1 columns)
     T tmin_w, tmax_w;                   // world depth range of the column
-    T margin;                           // largest |t'| in the cell
+    T margin_c;                         // largest |t'| in the cell, in units of the voxel height c
 };
 
-// Classification of the corner lines of one column's footprint (identical in every lane of
-// a warp that handles the column): elements k_first .. k_first + ng carry weight, the
-// crossing lines are k_first + 1 .. k_first + ng.
+// Classification of the corner lines of one column's footprint, computed cooperatively by
+// the 32 lanes of a warp (the result is identical in every lane): the four cell corners are
+// projected by lane groups of four, the lines k0 .. k1+1 of the footprint are classified one
+// per lane, and ballots give the first and last line that is not of the "before" / "after"
+// type.  Elements k_first .. k_first + ng carry weight, the crossing lines are
+// k_first + 1 .. k_first + ng.
 template <typename T>
-__device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy, ColumnView<T>& cv) {
+__device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy, int lane, ColumnView<T>& cv) {
     using L = typename LineOf<T>::type;
     const T a = G3<T>::a(g), b = G3<T>::b(g);
-    const T X0 = G3<T>::x0(g) + ix * a, X1 = X0 + a, Y0 = G3<T>::y0(g) + iy * b, Y1 = Y0 + b;
+    const T X0 = G3<T>::x0(g) + ix * a, Y0 = G3<T>::y0(g) + iy * b;
     const T cs = G3<T>::cs(g, v, 0), sn = G3<T>::cs(g, v, 1);
     const T s = G3<T>::s(g), D = G3<T>::sdd(g);
-    T umin = T(1e30), umax = T(-1e30), tmin = T(1e30), tmax = T(-1e30);
+    const int qd = lane & 3;
+    const T X = X0 + ((qd & 1) ? a : T(0)), Y = Y0 + ((qd & 2) ? b : T(0));
+    const T t = s - X * cs - Y * sn;
+    const T u = G3<T>::div(D * (Y * cs - X * sn), t);
+    T umin = u, umax = u, tmin = t, tmax = t;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const T X = (q & 1) ? X1 : X0, Y = (q & 2) ? Y1 : Y0;
-        const T t = s - X * cs - Y * sn;
-        const T u = G3<T>::div(D * (Y * cs - X * sn), t);
-        umin = u < umin ? u : umin;
-        umax = u > umax ? u : umax;
-        tmin = t < tmin ? t : tmin;
-        tmax = t > tmax ? t : tmax;
+    for (int o = 1; o <= 2; o <<= 1) {
+        const T u2 = __shfl_xor_sync(0xffffffffu, umin, o), u3 = __shfl_xor_sync(0xffffffffu, umax, o);
+        const T t2 = __shfl_xor_sync(0xffffffffu, tmin, o), t3 = __shfl_xor_sync(0xffffffffu, tmax, o);
+        umin = u2 < umin ? u2 : umin;
+        umax = u3 > umax ? u3 : umax;
+        tmin = t2 < tmin ? t2 : tmin;
+        tmax = t3 > tmax ? t3 : tmax;
     }
     cv.tmin_w = tmin;
     cv.tmax_w = tmax;
-    cv.margin = T(0.5) * (fabs(a * cs) + fabs(b * sn));
-    const T idu = T(1) / G3<T>::du(g);
+    cv.margin_c = T(0.5) * (fabs(a * cs) + fabs(b * sn)) * G3<T>::ic(g);
+    const T idu = G3<T>::idu(g);
     T f0 = floor((umin - G3<T>::u0(g)) * idu - G3<T>::eps), f1 = floor((umax - G3<T>::u0(g)) * idu + G3<T>::eps);
     cv.ok = 0;
     if (f1 < T(0) || f0 > T(g.nu - 1)) return;
@@ -332,20 +392,20 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
     cv.axis = axis;
     cv.sigma = sigma;
     const int w = axis == 0 ? ix : iy, cc = axis == 0 ? iy : ix;
-    // lines k0 .. k1+1 in order; "before" type: empty for sigma > 0, whole cell for sigma < 0
-    int ga = -1, gb = -1;
-    for (int k = k0; k <= k1 + 1; ++k) {
+    // line k0 + lane; "before" type: empty for sigma > 0, whole cell for sigma < 0
+    bool not_before = false, not_after = false;
+    if (lane <= k1 + 1 - k0) {
         L line;
-        line.load(g, v, k, w);
+        line.load(g, v, k0 + lane, w);
         T y0, y1;
         line.offsets(cc, y0, y1);
         const bool empty = y0 <= T(0) && y1 <= T(0), full = y0 >= T(1) && y1 >= T(1);
-        const bool before = sigma > 0 ? empty : full, after = sigma > 0 ? full : empty;
-        if (ga < 0 && !before) ga = k;
-        if (!after) gb = k;
+        not_before = !(sigma > 0 ? empty : full);
+        not_after = !(sigma > 0 ? full : empty);
     }
-    if (ga < 0) ga = k1 + 2;              // every line of the footprint is of the "before" type
-    if (gb < 0) gb = k0 - 1;              // every line is of the "after" type
+    const unsigned mb = __ballot_sync(0xffffffffu, not_before), ma = __ballot_sync(0xffffffffu, not_after);
+    const int ga = mb ? k0 + __ffs(mb) - 1 : k1 + 2;     // every line is of the "before" type
+    int gb = ma ? k0 + 31 - __clz(ma) : k0 - 1;          // every line is of the "after" type
     if (gb < ga - 1) gb = ga - 1;
     int ng = gb - ga + 1;
     ng = ng > kMaxG ? kMaxG : ng;          // excluded by the geometry check
@@ -354,26 +414,49 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
     cv.ok = 1;
 }
 
-// Atom of crossing line i (0 <= i < cv.ng) of the column.
+// Voxels of the grid that the detector's rows can reach from a column with world depth range
+// [tmin, tmax] (conservative by one voxel on each side; the exact row range of each voxel is
+// decided by voxel_rows).
 template <typename T>
-__device__ __forceinline__ void crossing_atom(const Geo& g, int v, int ix, int iy, const ColumnView<T>& cv, int i,
-                                              AtomE<T>& P) {
+__device__ __forceinline__ void cone_z_range(const Geo& g, T tmin, T tmax, int& izlo, int& izhi) {
+    const T D = G3<T>::sdd(g), vb = G3<T>::v0(g), vt = vb + T(g.nv) * G3<T>::dv(g);
+    const T zmin = G3<T>::div(vb * (vb < T(0) ? tmax : tmin), D);
+    const T zmax = G3<T>::div(vt * (vt > T(0) ? tmax : tmin), D);
+    const T ic = G3<T>::ic(g);
+    T lo = floor((zmin - G3<T>::z0(g)) * ic) - T(1), hi = floor((zmax - G3<T>::z0(g)) * ic) + T(1);
+    lo = lo < T(0) ? T(0) : lo;
+    hi = hi > T(g.nz - 1) ? T(g.nz - 1) : hi;
+    izlo = (int)lo;
+    izhi = hi < lo ? izlo - 1 : (int)hi;
+}
+
+// Piece p of the table of atom i of the column: crossing line i for 0 <= i < cv.ng, the whole
+// cell for i = cv.ng (a line above the cell).  One code path for both, so that the lanes
+// building them do not diverge.
+template <typename T>
+__device__ __forceinline__ void column_piece(const Geo& g, int v, int ix, int iy, const ColumnView<T>& cv, int i,
+                                             int p, AtomP<T>& P) {
     using L = typename LineOf<T>::type;
     const int axis = cv.axis;
     const int w = axis == 0 ? ix : iy, cc = axis == 0 ? iy : ix;
     const T a = G3<T>::a(g), b = G3<T>::b(g);
-    L line;
-    line.load(g, v, cv.k_first + 1 + i, w);
-    T y0, y1;
-    line.offsets(cc, y0, y1);
-    make_atom_e<T>(P, y0, y1, axis == 0 ? a : b, axis == 0 ? b : a, axis, G3<T>::cs(g, v, 0), G3<T>::cs(g, v, 1));
+    T y0 = T(2), y1 = T(2);
+    if (i < cv.ng) {
+        L line;
+        line.load(g, v, cv.k_first + 1 + i, w);
+        line.offsets(cc, y0, y1);
+    }
+    build_piece<T>(P, p, y0, y1, axis == 0 ? a : b, axis == 0 ? b : a, axis, G3<T>::cs(g, v, 0), G3<T>::cs(g, v, 1));
 }
 
+// Builds the tables of the column's ng + 1 atoms, one (atom, piece) per lane.
 template <typename T>
-__device__ __forceinline__ void full_atom(const Geo& g, int v, AtomE<T>& P) {
-    const int axis = g.axis_sigma[2 * v];
-    const T a = G3<T>::a(g), b = G3<T>::b(g);
-    make_atom_e<T>(P, T(2), T(2), axis == 0 ? a : b, axis == 0 ? b : a, axis, G3<T>::cs(g, v, 0), G3<T>::cs(g, v, 1));
+__device__ __forceinline__ void column_atoms(const Geo& g, int v, int ix, int iy, const ColumnView<T>& cv, int lane,
+                                             AtomP<T>* atoms) {
+    for (int it = lane; it < (cv.ng + 1) * 5; it += 32) {
+        const int i = it / 5, p = it - 5 * i + 1;
+        column_piece<T>(g, v, ix, iy, cv, i, p, atoms[i == cv.ng ? kMaxG : i]);
+    }
 }
 
 // Rows of voxel [z0w, z1w] (world) seen from a column with depth range [tmin, tmax].
@@ -382,7 +465,7 @@ __device__ __forceinline__ bool voxel_rows(const Geo& g, T z0w, T z1w, T tmin, T
     const T D = G3<T>::sdd(g);
     const T vlo = D * (z0w < T(0) ? G3<T>::div(z0w, tmin) : G3<T>::div(z0w, tmax));
     const T vhi = D * (z1w > T(0) ? G3<T>::div(z1w, tmin) : G3<T>::div(z1w, tmax));
-    const T idv = T(1) / G3<T>::dv(g);
+    const T idv = G3<T>::idv(g);
     T h0 = floor((vlo - G3<T>::v0(g)) * idv - G3<T>::eps), h1 = floor((vhi - G3<T>::v0(g)) * idv + G3<T>::eps);
     if (h1 < T(0) || h0 > T(g.nv - 1)) return false;
     l0 = h0 < T(0) ? 0 : (int)h0;
@@ -396,7 +479,7 @@ __device__ __forceinline__ bool voxel_rows(const Geo& g, T z0w, T z1w, T tmin, T
 // Phi per atom on two consecutive row corner planes.
 template <typename T, typename Emit>
 __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int iy, int iz, const ColumnView<T>& cv,
-                                              const AtomE<T>* atoms, const AtomE<T>& full, T* scratch, Emit&& emit) {
+                                              const AtomP<T>* atoms, const AtomP<T>& full, T* scratch, Emit&& emit) {
     using R = typename RowOf<T>::type;
     const T c = G3<T>::c(g);
     const T z0w = G3<T>::z0(g) + iz * c;
@@ -413,13 +496,13 @@ __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int i
         row.at(g, v, r, ix, iy);
         const T h = row.rel(iz);                 // plane height above the voxel bottom, units of c
         const T q = G3<T>::q(g, r);
-        const T m = fabs(q) * cv.margin / c;     // height change across the cell, units of c
+        const T m = fabs(q) * cv.margin_c;       // height change across the cell, units of c
         const int cls = h + m <= T(0) ? 0 : (h - m >= T(1) ? 2 : 1);   // below / above / crossing
         const T gw = h * c, iq = q != T(0) ? G3<T>::div(T(1), fabs(q)) : T(0);
 #pragma unroll 1
         for (int j = 0; j < na; ++j) {
-            const AtomE<T>& P = j == 0 ? full : atoms[j - 1];
-            PHI(cur, j) = cls == 0 ? T(0) : (cls == 2 ? c * P.A : phi_e<T>(P, gw, q, iq, c));
+            const AtomP<T>& P = j == 0 ? full : atoms[j - 1];
+            PHI(cur, j) = cls == 0 ? T(0) : (cls == 2 ? c * P.A : phi_p<T>(P, gw, q, iq, c));
         }
         if (r == l0) continue;
         // W(k, l) = sigma [S(k+1) - S(k)] with S = 0 (empty lines), S_full (whole-cell lines)
@@ -440,52 +523,65 @@ __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int i
 }
 
 // ---------------------------------------------------------------------------------------
-// Back projection: one warp per voxel column and window of 32 voxels in z (one voxel per
-// lane).  All lanes of a warp share the column's view geometry: per view the lanes classify
-// the footprint's corner lines identically, lanes 0 .. ng-1 build the crossing lines' atoms
-// in parallel (warp-private shared memory) and the last lane the whole-cell atom; then each
-// lane forms its voxel's entries and accumulates W p.
+// Back projection: one warp per voxel column and window of ZW voxels in z (ZW = 64, 128 or
+// 256, the largest that still gives the grid enough warps).  All lanes of a
+// warp share the column's view geometry: per view the warp classifies the footprint's corner
+// lines, lanes 0 .. ng build the column's atoms in parallel (warp-private shared memory),
+// then the voxels of the window that the view's cone reaches are dealt to the lanes in
+// order (32 at a time), each lane forming its voxel's entries and adding W p to the voxel's
+// sum in shared memory.  The sums are written once at the end.
 // ---------------------------------------------------------------------------------------
-constexpr int BW = 4;   // warps (columns) per block
+constexpr int BW = 4;     // warps (columns) per block
+constexpr int ZWN = 64;   // voxels of a column per warp in the nnz count
 
-template <typename T, int NB>
+template <typename T, int NB, int ZW>
 __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
                                                       int B, int b_off, T scale, int accumulate) {
-    __shared__ AtomE<T> atoms_s[BW][kMaxG + 1];
+    __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
     __shared__ T scratch_s[BW][2 * (kMaxG + 1) * 32];
+    __shared__ T acc_s[BW][NB * ZW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;                       // whole warp leaves together
     const int ix = col % g.nx, iy = col / g.nx;
-    const int iz = blockIdx.y * 32 + lane;
-    AtomE<T>* atoms = atoms_s[wid];
-    AtomE<T>& full = atoms_s[wid][kMaxG];
+    const int zb = blockIdx.y * ZW, ze = min(zb + ZW, g.nz);
+    AtomP<T>* atoms = atoms_s[wid];
     T* scratch = scratch_s[wid] + lane;
-    T acc[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) acc[i] = T(0);
+    T* acc = acc_s[wid];                                  // acc[b * ZW + (iz - zb)]
+    for (int i = lane; i < NB * ZW; i += 32) acc[i] = T(0);
     for (int v = 0; v < g.n_views; ++v) {
         ColumnView<T> cv;
-        column_view<T>(g, v, ix, iy, cv);
+        column_view<T>(g, v, ix, iy, lane, cv);
         if (!cv.ok) continue;                              // warp-uniform
+        int z0, z1;
+        cone_z_range<T>(g, cv.tmin_w, cv.tmax_w, z0, z1);
+        z0 = max(z0, zb);
+        z1 = min(z1, ze - 1);
+        if (z0 > z1) continue;
         __syncwarp();
-        if (lane < cv.ng) crossing_atom<T>(g, v, ix, iy, cv, lane, atoms[lane]);
-        if (lane == 31) full_atom<T>(g, v, full);
+        column_atoms<T>(g, v, ix, iy, cv, lane, atoms);
         __syncwarp();
-        if (iz < g.nz) {
-            const T* pv = ps + (size_t)v * g.nv * g.nu * NB;
-            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, full, scratch, [&](int k, int l, T wt) {
-                fma_vec<T, NB>(acc, wt, pv + ((size_t)l * g.nu + k) * NB);
+        const T* pv = ps + (size_t)v * g.nv * g.nu * NB;
+        for (int iz = z0 + lane; iz <= z1; iz += 32) {
+            T sum[NB];
+#pragma unroll
+            for (int i = 0; i < NB; ++i) sum[i] = T(0);
+            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, [&](int k, int l, T wt) {
+                fma_vec<T, NB>(sum, wt, pv + ((size_t)l * g.nu + k) * NB);
             });
+#pragma unroll
+            for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sum[i];
         }
     }
-    if (iz >= g.nz) return;
+    __syncwarp();
     const size_t nvox = (size_t)g.nx * g.ny * g.nz;
-    const size_t vox = ((size_t)iz * g.ny + iy) * g.nx + ix;
+    for (int iz = zb + lane; iz < ze; iz += 32) {
+        const size_t vox = ((size_t)iz * g.ny + iy) * g.nx + ix;
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-        const int bidx = b_off + i;
-        if (bidx < B) store_any3<T>(x, (size_t)bidx * nvox + vox, xdt, acc[i] * scale, accumulate != 0);
+        for (int i = 0; i < NB; ++i) {
+            const int bidx = b_off + i;
+            if (bidx < B) store_any3<T>(x, (size_t)bidx * nvox + vox, xdt, acc[i * ZW + iz - zb] * scale, accumulate != 0);
+        }
     }
 }
 
@@ -504,7 +600,7 @@ template <typename T, int NB>
 __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __restrict__ xs0, const T* __restrict__ xs1,
                                                     void* __restrict__ p, int pdt, int B, int b_off, T scale,
                                                     int accumulate) {
-    __shared__ AtomE<T> atoms_s[FW][2];
+    __shared__ AtomP<T> atoms_s[FW][3];   // line k, line k+1, whole cell
     __shared__ T rows_s[FW][RWMAX * NB];
     using L = typename LineOf<T>::type;
     using R = typename RowOf<T>::type;
@@ -521,16 +617,16 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
     const T a = G3<T>::a(g), b = G3<T>::b(g), c = G3<T>::c(g);
     const T hw = axis == 0 ? a : b, hc = axis == 0 ? b : a;
-    const T cs = G3<T>::cs(g, v, 0), sn = G3<T>::cs(g, v, 1);
-    const T margin = T(0.5) * (fabs(a * cs) + fabs(b * sn));
+    const T cs = G3<T>::cs(g, v, 0), sn = G3<T>::cs(g, v, 1), s = G3<T>::s(g);
+    const T margin_c = T(0.5) * (fabs(a * cs) + fabs(b * sn)) * G3<T>::ic(g);   // units of c
     const T q_lo = G3<T>::q(g, L0), q_hi = G3<T>::q(g, L0 + nrow);
-    const T mz = (fabs(q_lo) > fabs(q_hi) ? fabs(q_lo) : fabs(q_hi)) * margin / c + T(1e-3);
+    const T mz = (fabs(q_lo) > fabs(q_hi) ? fabs(q_lo) : fabs(q_hi)) * margin_c + T(1e-3);
     const int w0 = g.wrange[2 * ((size_t)v * g.nu + k)], w1 = g.wrange[2 * ((size_t)v * g.nu + k) + 1];
     L la, lb;
     la.load(g, v, k, w0);
     lb.load(g, v, k + 1, w0);
-    AtomE<T>& Pa = atoms_s[wid][0];
-    AtomE<T>& Pb = atoms_s[wid][1];
+    // the whole-cell atom is the same in every cell of the view: built once
+    if (lane < 5) build_piece<T>(atoms_s[wid][2], lane + 1, T(2), T(2), hw, hc, axis, cs, sn);
     __syncwarp();
     for (int w = w0; w < w1; ++w) {
         int clo = min(la.cell_lo(), lb.cell_lo());
@@ -552,11 +648,39 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
             if (zhi < T(0) || zlo > T(g.nz - 1)) continue;
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
-            __syncwarp();
-            if (lane == 0 && !ea) make_atom_e<T>(Pa, a0, a1, hw, hc, axis, cs, sn);
-            if (lane == 1 && !eb) make_atom_e<T>(Pb, b0, b1, hw, hc, axis, cs, sn);
-            __syncwarp();
             const T* xcol = xs + ((size_t)w * g.nz) * nc * NB + (size_t)cc * NB;
+            // cells whose voxels in reach are all zero add nothing: skip them before any atom
+            // is built
+            bool nzv = false;
+            for (int zb = izlo; zb <= izhi && !__any_sync(0xffffffffu, nzv); zb += 32) {
+                const int iz = zb + lane;
+                if (iz <= izhi) {
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) nzv |= __ldg(xcol + (size_t)iz * nc * NB + i) != T(0);
+                }
+            }
+            if (!__any_sync(0xffffffffu, nzv)) continue;
+            // atoms of the crossing lines (a line above the cell uses the whole-cell atom)
+            __syncwarp();
+            if (lane < 10) {                                // (line, piece) per lane
+                const int j = lane >= 5 ? 1 : 0, pc = lane - 5 * j + 1;
+                if (j ? !(eb || fb) : !(ea || fa))
+                    build_piece<T>(atoms_s[wid][j], pc, j ? b0 : a0, j ? b1 : a1, hw, hc, axis, cs, sn);
+            }
+            __syncwarp();
+            const AtomP<T>& Pa = atoms_s[wid][fa ? 2 : 0];
+            const AtomP<T>& Pb = atoms_s[wid][fb ? 2 : 1];
+            // depth range of the column (the same for all its voxels)
+            T tmin = T(1e30), tmax = T(-1e30);
+            {
+                const T X0 = G3<T>::x0(g) + ix * a, Y0 = G3<T>::y0(g) + iy * b;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const T t = s - (X0 + ((qq & 1) ? a : T(0))) * cs - (Y0 + ((qq & 2) ? b : T(0))) * sn;
+                    tmin = t < tmin ? t : tmin;
+                    tmax = t > tmax ? t : tmax;
+                }
+            }
             for (int zb = izlo; zb <= izhi; zb += 32) {
                 const int iz = zb + lane;
                 if (iz > izhi) continue;
@@ -568,21 +692,10 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                     any |= xv[i] != T(0);
                 }
                 if (!any) continue;
-                int l0, l1;
                 // rows of this voxel at this cell, clipped to the window
-                {
-                    const T z0w = G3<T>::z0(g) + iz * c;
-                    const T s = G3<T>::s(g);
-                    T tmin = T(1e30), tmax = T(-1e30);
-                    const T X0 = G3<T>::x0(g) + ix * a, Y0 = G3<T>::y0(g) + iy * b;
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        const T t = s - (X0 + ((qq & 1) ? a : T(0))) * cs - (Y0 + ((qq & 2) ? b : T(0))) * sn;
-                        tmin = t < tmin ? t : tmin;
-                        tmax = t > tmax ? t : tmax;
-                    }
-                    if (!voxel_rows<T>(g, z0w, z0w + c, tmin, tmax, l0, l1)) continue;
-                }
+                const T z0w = G3<T>::z0(g) + iz * c;
+                int l0, l1;
+                if (!voxel_rows<T>(g, z0w, z0w + c, tmin, tmax, l0, l1)) continue;
                 if (l1 < L0 || l0 >= L0 + nrow) continue;
                 // Phi of both lines at corners l0 .. l1+1; entries of rows in the window
                 T pa = T(0), pb = T(0);
@@ -591,7 +704,7 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                     row.at(g, v, r, ix, iy);
                     const T h = row.rel(iz);
                     const T q = G3<T>::q(g, r);
-                    const T m = fabs(q) * margin / c;
+                    const T m = fabs(q) * margin_c;
                     T ca, cb;
                     if (h + m <= T(0)) {
                         ca = T(0);
@@ -601,8 +714,8 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                         cb = eb ? T(0) : c * Pb.A;
                     } else {
                         const T gw = h * c, iq = q != T(0) ? G3<T>::div(T(1), fabs(q)) : T(0);
-                        ca = ea ? T(0) : phi_e<T>(Pa, gw, q, iq, c);
-                        cb = eb ? T(0) : phi_e<T>(Pb, gw, q, iq, c);
+                        ca = ea ? T(0) : phi_p<T>(Pa, gw, q, iq, c);
+                        cb = eb ? T(0) : phi_p<T>(Pb, gw, q, iq, c);
                     }
                     if (r > l0) {
                         const int l = r - 1;
@@ -638,28 +751,31 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
 // Number of (voxel, view, element) whose volume exceeds 1e-6 of the voxel's (column-warps as
 // in the back projection).
 __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long long* counter) {
-    __shared__ AtomE<float> atoms_s[BW][kMaxG + 1];
+    __shared__ AtomP<float> atoms_s[BW][kMaxG + 1];
     __shared__ float scratch_s[BW][2 * (kMaxG + 1) * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;
     const int ix = col % g.nx, iy = col / g.nx;
-    const int iz = blockIdx.y * 32 + lane;
-    AtomE<float>* atoms = atoms_s[wid];
-    AtomE<float>& full = atoms_s[wid][kMaxG];
+    const int zb = blockIdx.y * ZWN, ze = min(zb + ZWN, g.nz);
+    AtomP<float>* atoms = atoms_s[wid];
     float* scratch = scratch_s[wid] + lane;
     const float thr = 1e-6f * g.a * g.b * g.c;
     unsigned long long cnt = 0;
     for (int v = 0; v < g.n_views; ++v) {
         ColumnView<float> cv;
-        column_view<float>(g, v, ix, iy, cv);
+        column_view<float>(g, v, ix, iy, lane, cv);
         if (!cv.ok) continue;
+        int z0, z1;
+        cone_z_range<float>(g, cv.tmin_w, cv.tmax_w, z0, z1);
+        z0 = max(z0, zb);
+        z1 = min(z1, ze - 1);
+        if (z0 > z1) continue;
         __syncwarp();
-        if (lane < cv.ng) crossing_atom<float>(g, v, ix, iy, cv, lane, atoms[lane]);
-        if (lane == 31) full_atom<float>(g, v, full);
+        column_atoms<float>(g, v, ix, iy, cv, lane, atoms);
         __syncwarp();
-        if (iz < g.nz)
-            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, full, scratch,
+        for (int iz = z0 + lane; iz <= z1; iz += 32)
+            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch,
                                  [&](int, int, float wt) { cnt += fabsf(wt) > thr; });
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
@@ -701,6 +817,25 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     return CSM_OK;
 }
 
+// Window height of the back projection: the largest of 256 (FP32 only), 128, 64 that is not
+// taller than the grid and still leaves one warp per SM lane group (152 SMs x 32 warps).
+static int back_window(const csm_geom_s* g, bool dbl) {
+    const size_t ncol = (size_t)g->nx * g->ny;
+    for (int zw = dbl ? 128 : 256; zw > 64; zw >>= 1)
+        if (g->nz > zw / 2 && ncol * (size_t)((g->nz + zw - 1) / zw) >= 152 * 32) return zw;
+    return 64;
+}
+
+template <typename T, int NB, int ZW>
+static csm_status launch_back3(const Geo& g, const csm_geom_s* gh, const T* ps, void* x, int64_t batch,
+                               csm_dtype xdt, int64_t b0, T scale, int flags, cudaStream_t st) {
+    const size_t ncol = (size_t)gh->nx * gh->ny;
+    dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZW - 1) / ZW);
+    back3d_vox<T, NB, ZW><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
+                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
+    return check_launch();
+}
+
 template <typename T, int NB>
 static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_t batch, csm_dtype pdt,
                             csm_dtype xdt, int flags, void* ws, cudaStream_t st) {
@@ -708,13 +843,13 @@ static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_
     T* ps = (T*)ws;
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
     const size_t n = (size_t)gh->n_views * gh->nv * gh->nu;
-    const size_t ncol = (size_t)gh->nx * gh->ny;
+    const int zw = back_window(gh, sizeof(T) == 8);
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         prep_sino_3d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (int)pdt, (int)batch, (int)b0, n, ps);
-        dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + 31) / 32);
-        back3d_vox<T, NB><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
-                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
-        csm_status r = check_launch();
+        csm_status r;
+        if (sizeof(T) == 4 && zw == 256) r = launch_back3<T, NB, (sizeof(T) == 4 ? 256 : 128)>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
+        else if (zw == 128) r = launch_back3<T, NB, 128>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
+        else r = launch_back3<T, NB, 64>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
         if (r != CSM_OK) return r;
     }
     return CSM_OK;
@@ -740,7 +875,7 @@ csm_status back_3d(const csm_geom_s* g, const void* p, void* x, int64_t batch, c
                    int flags, void* ws, size_t ws_bytes, cudaStream_t st) {
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     if (!ws || ws_bytes < workspace_3d(g, 1, batch, dbl)) return CSM_EINVAL;
-    if ((g->nz + 31) / 32 > 65535) return CSM_EUNSUPPORTED;
+    if ((g->nz + 63) / 64 > 65535) return CSM_EUNSUPPORTED;
     switch (chunk3(batch)) {
         case 4: return dbl ? run_back3<double, 4>(g, p, x, batch, pdt, xdt, flags, ws, st)
                            : run_back3<float, 4>(g, p, x, batch, pdt, xdt, flags, ws, st);
@@ -756,7 +891,7 @@ csm_status nnz_3d(const csm_geom_s* gh, int64_t* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(gh->t.counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     const size_t ncol = (size_t)gh->nx * gh->ny;
-    dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + 31) / 32);
+    dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZWN - 1) / ZWN);
     nnz3d_kernel<<<bg, bb, 0, st>>>(g, gh->t.counter);
     csm_status s = check_launch();
     if (s != CSM_OK) return s;
