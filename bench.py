@@ -386,31 +386,51 @@ def run_serving(args, rank, world, local):
         solve_alone(r, device=dev)
         torch.cuda.synchronize()
         service.append(time.perf_counter() - t0)
+    n = len(reqs)
+    # throughput: every request waiting at t = 0; the unbatched server takes them one by one
+    srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
+    t0 = time.perf_counter()
+    srv.serve(reqs, realtime=False)
+    makespan = time.perf_counter() - t0
+    results_sat = [r.result for r in reqs]
+    # latency: Poisson arrivals at `load` times the unbatched capacity
     cap = 1.0 / float(np.mean(service))
     rate = args.load * cap
     rng = np.random.default_rng(1)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     for r, a in zip(reqs, arrivals):
         r.arrival = float(a)
+        r.result = None
     base_lat = fifo_latencies(arrivals, service)
-    base_makespan = max(a + l for a, l in zip(arrivals, base_lat))
     srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
-    t0 = time.perf_counter()
     done = srv.serve(reqs, realtime=True)
-    makespan = time.perf_counter() - t0
     lat = [r.latency for r in done]
     st, bst = latency_stats(lat), latency_stats(base_lat)
+    same = all(np.array_equal(a, r.result) or np.allclose(a, r.result, rtol=1e-4, atol=1e-6)
+               for a, r in zip(results_sat, reqs))
+    kinds = np.array([r.geom["dim"] for r in reqs])
+    lat_a, blat_a = np.array(lat), np.array(base_lat)
     line = {
-        "metric": METRIC, "value": len(done) / makespan, "unit": "requests/s", "n_gpus": 1,
+        "metric": METRIC, "value": n / makespan, "unit": "requests/s", "n_gpus": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "serving", "requests": len(done), "share_2d": sum(r.geom["dim"] == 2 for r in done) / len(done),
+        "config": {"workload": "serving", "requests": n, "share_2d": float((kinds == 2).mean()),
                    "nag_iterations": 20, "power_iterations": 20, "budget_gb": 120, "max_active": 16,
+                   "priority_levels": len(srv.levels),
                    "arrival_rate_per_s": rate, "load_vs_capacity": args.load},
+        "throughput": {"served_requests_per_s": n / makespan, "unbatched_requests_per_s": n / float(np.sum(service)),
+                       "served_makespan_s": makespan, "unbatched_makespan_s": float(np.sum(service)),
+                       "note": "all requests waiting at t = 0"},
         "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
-        "unbatched": {"requests_per_s": len(done) / base_makespan, "p50_s": bst["p50_s"], "p99_s": bst["p99_s"],
+        "p50_2d_s": float(np.median(lat_a[kinds == 2])) if (kinds == 2).any() else None,
+        "p50_3d_s": float(np.median(lat_a[kinds == 3])) if (kinds == 3).any() else None,
+        "unbatched": {"p50_s": bst["p50_s"], "p99_s": bst["p99_s"], "mean_s": bst["mean_s"],
+                      "p50_2d_s": float(np.median(blat_a[kinds == 2])) if (kinds == 2).any() else None,
+                      "p50_3d_s": float(np.median(blat_a[kinds == 3])) if (kinds == 3).any() else None,
                       "mean_service_s": float(np.mean(service)),
                       "note": "same requests and arrivals, one at a time with plain csm_forward/csm_back calls "
                               "(FIFO queue over the measured service times)"},
+        "results_equal_across_runs": bool(same),
+        "service_s": [round(float(x), 4) for x in service],
     }
     print(json.dumps(line), flush=True)
 

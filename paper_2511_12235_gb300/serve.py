@@ -5,18 +5,27 @@ number of NAG iterations on the Tikhonov objective (Section "Numerical Experimen
 Eq. (exp_tikh)).  The server
 
 * admits requests in arrival order while their device-memory footprint fits a budget
-  (120 GB by default) and a slot is free; requests that arrive while others run are admitted
-  as soon as memory and slots free up;
+  (120 GB by default) and a slot of their cost class is free; requests that arrive while
+  others run are admitted as soon as memory and slots free up (a request waiting for a slot
+  of its class does not hold back cheaper ones; one waiting for memory holds back all later
+  ones, so that none starves);
 * runs every admitted request on its own CUDA stream, so the projections of different
-  requests overlap on the GPU;
+  requests overlap on the GPU; the stream's priority follows the request's estimated cost
+  (cheapest requests highest), so the block scheduler starts the blocks of short requests
+  before the remaining blocks of long ones: a small request does not wait for a large one to
+  drain, which is what a FIFO of whole requests would make it do.  The costlier a class, the
+  fewer of its requests run at once (16, 4, 2, 1 for the four classes by default): one large
+  3D solve already fills the GPU, and large requests sharing it would all finish late;
 * estimates ||W|| by power iteration on the device (the scalar never leaves the GPU), then
   captures the request's NAG iterations once into a CUDA graph and replays it: the whole
   solve is a single launch;
 * polls completion events and returns results with their latency.
 
 All device work is in the library's kernels; the server only orders it.  Results do not
-depend on which other requests run at the same time: every kernel has a fixed reduction
-order and no atomics.
+depend on which other requests run at the same time beyond rounding: every kernel sees only
+its own request's data, the 2D kernels and all reductions have a fixed order (bit-identical
+results), and the 3D forward adds the entries of one detector row through shared-memory
+atomics of one warp, whose order can change the last bits of an FP32 sum.
 """
 from __future__ import annotations
 
@@ -27,6 +36,7 @@ import numpy as np
 import torch
 
 from .projector import Projector
+from .sched import admit_order
 from .solvers import NAG, power_norm2_device
 
 
@@ -49,6 +59,23 @@ class Request:
         return self.t_done - self.arrival
 
 
+def cost_estimate(geom: dict, iters: int, power_iters: int) -> float:
+    """Relative device work of a request: projector calls x views x voxels x the entries per
+    voxel and view (about 2.5 elements in 2D, 6 elements in 3D)."""
+    nvox = geom["nx"] * geom["ny"] * geom.get("nz", 1)
+    per = 6.0 if geom.get("dim", 2) == 3 else 2.5
+    return 2.0 * (iters + power_iters + 1) * geom["n_views"] * nvox * per
+
+
+def priority_range():
+    """(lowest, highest) stream priority of the device (a lower number is a higher priority)."""
+    fn = getattr(torch.cuda.Stream, "priority_range", None)
+    if fn is not None:
+        lo, hi = fn()
+        return int(lo), int(hi)
+    return 0, -1
+
+
 def footprint_bytes(geom: dict, elem: int = 4) -> int:
     """Device memory a request holds: NAG state u, y, g (3 volumes), residual and data
     (2 sinograms), power-iteration vectors (2 volumes, 1 sinogram), the projector's
@@ -66,20 +93,47 @@ class _Active:
 
 
 class ReconServer:
+    """budget_bytes: device memory the admitted requests may hold; max_active: requests on
+    the GPU at once; priorities: order streams by request cost (else all at one priority);
+    cost_edges: cost thresholds between priority levels (default: decades of
+    ``cost_estimate`` from 1e10, the cheapest level highest); level_caps: requests of each
+    level (highest first) that may run at once."""
+
     def __init__(self, device="cuda:0", budget_bytes: int = 120 << 30, max_active: int = 16,
-                 use_graphs: bool = True):
+                 use_graphs: bool = True, priorities: bool = True, cost_edges=None, level_caps=None):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.max_active = int(max_active)
         self.use_graphs = use_graphs
-        self.streams = [torch.cuda.Stream(device=self.device) for _ in range(self.max_active)]
-        self.free_streams = list(range(self.max_active))
+        lo, hi = priority_range() if priorities else (0, 0)
+        hi = max(hi, lo - 3)                                  # at most four levels
+        self.levels = list(range(hi, lo + 1))               # highest priority first
+        self.cost_edges = list(cost_edges) if cost_edges is not None else \
+            [10.0 ** e for e in range(10, 10 + len(self.levels) - 1)]
+        # one stream per slot and level, created up front so that no two admitted requests
+        # ever share a stream
+        self.pool = {lv: [torch.cuda.Stream(device=self.device, priority=lv) for _ in range(self.max_active)]
+                     for lv in self.levels}
+        if level_caps is None:
+            level_caps = [self.max_active, 4, 2, 1][:len(self.levels)]
+            if len(self.levels) > 1:
+                level_caps[-1] = 1
+        self.caps = {lv: max(1, min(int(c), self.max_active)) for lv, c in zip(self.levels, level_caps)}
+        self.running = {lv: 0 for lv in self.levels}
+        self.slots = self.max_active
         self._deferred = []          # projectors released once the device is idle
+
+    def level_of(self, req: Request) -> int:
+        c = cost_estimate(req.geom, req.iters, req.power_iters)
+        i = sum(1 for e in self.cost_edges if c >= e)
+        return self.levels[min(i, len(self.levels) - 1)]
 
     # -----------------------------------------------------------------------------------
     def _launch(self, req: Request, now: float) -> _Active:
-        si = self.free_streams.pop()
-        s = self.streams[si]
+        self.slots -= 1
+        lv = self.level_of(req)
+        self.running[lv] += 1
+        s = self.pool[lv].pop()
         g = req.geom
         with torch.cuda.device(self.device), torch.cuda.stream(s):
             P = Projector(g, device=self.device)
@@ -108,13 +162,16 @@ class ReconServer:
             done = torch.cuda.Event()
             done.record(s)
         req.t_admit = now
-        act = _Active(req, si, P, nag, graph, out_host, done, footprint_bytes(g))
+        act = _Active(req, (lv, s), P, nag, graph, out_host, done, footprint_bytes(g))
         return act
 
     def _finish(self, act: _Active, now: float):
         act.req.result = act.out_host.numpy().copy()
         act.req.t_done = now
-        self.free_streams.append(act.stream)
+        self.slots += 1
+        lv, s = act.stream
+        self.pool[lv].append(s)
+        self.running[lv] -= 1
         self._deferred.append(act.P)
         act.graph = None
         act.nag = None
@@ -139,17 +196,15 @@ class ReconServer:
         t0 = time.perf_counter()
         while pending or active:
             now = time.perf_counter() - t0
-            # admit in arrival order while memory and a slot are free
-            while pending and pending[0].arrival <= now and self.free_streams:
-                need = footprint_bytes(pending[0].geom)
-                if need > self.budget:
-                    raise ValueError("request %d needs %d bytes, more than the budget" % (pending[0].id, need))
-                if used + need > self.budget:
-                    break
-                req = pending.pop(0)
-                active.append(self._launch(req, now))
-                used += need
-                now = time.perf_counter() - t0
+            # admit in arrival order while memory and a slot of the request's class are free
+            idx = admit_order(pending, now, self.slots, self.running, self.caps, used, self.budget,
+                              self.level_of, lambda r: footprint_bytes(r.geom))
+            for i in idx:
+                req = pending[i]
+                active.append(self._launch(req, time.perf_counter() - t0))
+                used += footprint_bytes(req.geom)
+            for i in reversed(idx):
+                pending.pop(i)
             # completions
             still = []
             for act in active:

@@ -57,3 +57,18 @@ def test_alone_equals_mixed_and_budget():
     spans = sorted((r.t_admit, r.t_done) for r in done2 if 2 * footprint_bytes(r.geom) > biggest)
     for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
         assert b0 >= a1 - 1e-3
+
+
+def test_priority_follows_cost():
+    """Cheaper requests get streams of higher (numerically lower) priority."""
+    from paper_2511_12235_gb300.serve import ReconServer, Request, cost_estimate
+    srv = ReconServer(max_active=2, use_graphs=False)
+    small = synth.geometry(256, 256, 1, n_views=360, s=500.0, sdd=750.0, nu=384)
+    big = synth.geometry(256, 256, 256, n_views=360, s=500.0, sdd=750.0, nu=384, nv=384)
+    big["dim"] = 3
+    rs = Request(id=0, geom=small, sino=np.zeros(1, np.float32))
+    rb = Request(id=1, geom=big, sino=np.zeros(1, np.float32))
+    assert cost_estimate(small, 20, 20) < cost_estimate(big, 20, 20)
+    assert srv.level_of(rs) <= srv.level_of(rb)
+    if len(srv.levels) > 1:
+        assert srv.level_of(rs) < srv.level_of(rb)

@@ -1,0 +1,41 @@
+"""Admission logic of the serving loop (host only): arrival order, class caps, memory budget."""
+import dataclasses
+
+import pytest
+
+from paper_2511_12235_gb300.sched import admit_order  # noqa: E402
+
+
+@dataclasses.dataclass
+class R:
+    id: int
+    arrival: float
+    lv: int
+    need: int
+
+
+def _admit(pending, now=10.0, slots=8, running=None, caps=None, used=0, budget=100):
+    caps = caps or {0: 8, 1: 2, 2: 1}
+    running = running or {0: 0, 1: 0, 2: 0}
+    return admit_order(pending, now, slots, running, caps, used, budget, lambda r: r.lv, lambda r: r.need)
+
+
+def test_arrival_order_and_slots():
+    p = [R(i, float(i), 0, 1) for i in range(5)]
+    assert _admit(p, slots=3) == [0, 1, 2]
+    assert _admit(p, now=1.5) == [0, 1]          # not yet arrived
+
+
+def test_full_class_is_passed_over():
+    p = [R(0, 0.0, 2, 10), R(1, 1.0, 2, 10), R(2, 2.0, 0, 10)]
+    # class 2 allows one request at a time: the second waits, the cheap one behind it goes
+    assert _admit(p) == [0, 2]
+    assert _admit(p, running={0: 0, 1: 0, 2: 1}) == [2]
+
+
+def test_memory_blocks_later_requests():
+    p = [R(0, 0.0, 0, 60), R(1, 1.0, 0, 50), R(2, 2.0, 0, 10)]
+    # the second does not fit next to the first: nothing after it overtakes it
+    assert _admit(p) == [0]
+    with pytest.raises(ValueError):
+        _admit([R(0, 0.0, 0, 101)])
