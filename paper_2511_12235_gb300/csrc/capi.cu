@@ -42,7 +42,9 @@ Geo make_geo(const csm_geom_s* g) {
     o.axis_sigma = g->t.axis_sigma; o.cs_f = g->t.cs_f; o.cs_d = g->t.cs_d;
     o.line_fx = g->t.line_fx; o.line_d = g->t.line_d; o.inv_f = g->t.inv_f; o.inv_d = g->t.inv_d;
     o.wrange = g->t.wrange; o.rowq_f = g->t.rowq_f; o.rowq_d = g->t.rowq_d;
-    o.rowp_fx = g->t.rowp_fx; o.rowp_d = g->t.rowp_d;
+    o.rowq4 = g->t.rowq4;
+    o.colt_fx = g->t.colt_fx;
+    o.colt_d = g->t.colt_d;
     return o;
 }
 
@@ -171,26 +173,31 @@ static csm_status build_tables(csm_geom_s* g) {
         rowq_d[l] = vv / D;
         rowq_f[l] = (float)(vv / D);
     }
-    // row planes z = q_l t(P): height above the grid bottom at column centres, units of c
-    const size_t nrp = g->dim == 3 ? 3 * (size_t)V * (nv + 1) : 3;
-    std::vector<long long> rowp_fx(nrp, 0);
-    std::vector<double> rowp_d(nrp, 0.0);
+    // depth of column centres per view, t_c / c = T0 + ix Tx + iy Ty (32.32 fixed point and
+    // double), so that the kernels form it without FP64 arithmetic
+    const size_t nct = g->dim == 3 ? 3 * (size_t)V : 3;
+    std::vector<long long> colt_fx(nct, 0);
+    std::vector<double> colt_d(nct, 0.0);
     if (g->dim == 3) {
-        const double zb = -0.5 * g->nz * g->c;
         for (int v = 0; v < V; ++v) {
             const double c = cos(g->angles[v]), sn = sin(g->angles[v]);
-            const double t00 = s - (x0 + 0.5 * g->a) * c - (y0 + 0.5 * g->b) * sn;
-            for (int l = 0; l <= nv; ++l) {
-                const double q = rowq_d[l];
-                const double A = (q * t00 - zb) / g->c, Bx = -q * g->a * c / g->c, Cy = -q * g->b * sn / g->c;
-                const size_t e = 3 * ((size_t)v * (nv + 1) + l);
-                rowp_d[e] = A; rowp_d[e + 1] = Bx; rowp_d[e + 2] = Cy;
-                if (fabs(A) + fabs(Bx) * g->nx + fabs(Cy) * g->ny > kFar) return CSM_EGEOM;
-                rowp_fx[e] = llround(A * 4294967296.0);
-                rowp_fx[e + 1] = llround(Bx * 4294967296.0);
-                rowp_fx[e + 2] = llround(Cy * 4294967296.0);
-            }
+            const double T0 = (s - (x0 + 0.5 * g->a) * c - (y0 + 0.5 * g->b) * sn) / g->c;
+            const double Tx = -g->a * c / g->c, Ty = -g->b * sn / g->c;
+            if (fabs(T0) + fabs(Tx) * g->nx + fabs(Ty) * g->ny > kFar) return CSM_EGEOM;
+            colt_d[3 * v] = T0; colt_d[3 * v + 1] = Tx; colt_d[3 * v + 2] = Ty;
+            colt_fx[3 * v] = llround(T0 * 4294967296.0);
+            colt_fx[3 * v + 1] = llround(Tx * 4294967296.0);
+            colt_fx[3 * v + 2] = llround(Ty * 4294967296.0);
         }
+    }
+    // row corners as float pairs (q = hi + lo) with 1/|q|, for the FP32 height of a row plane
+    std::vector<float> rowq4(4 * (size_t)(nv + 1), 0.0f);
+    for (int l = 0; l <= nv; ++l) {
+        const double q = rowq_d[l];
+        const float hi = (float)q;
+        rowq4[4 * l] = hi;
+        rowq4[4 * l + 1] = (float)(q - (double)hi);
+        rowq4[4 * l + 2] = q != 0.0 ? (float)(1.0 / fabs(q)) : 0.0f;
     }
 
     // one device block for everything
@@ -206,8 +213,9 @@ static csm_status build_tables(csm_geom_s* g) {
     size_t o_wr = off; off += al(wrange.size() * sizeof(int));
     size_t o_rf = off; off += al(rowq_f.size() * sizeof(float));
     size_t o_rd = off; off += al(rowq_d.size() * sizeof(double));
-    size_t o_pfx = off; off += al(rowp_fx.size() * sizeof(long long));
-    size_t o_pd = off; off += al(rowp_d.size() * sizeof(double));
+    size_t o_q4 = off; off += al(rowq4.size() * sizeof(float));
+    size_t o_cfx = off; off += al(colt_fx.size() * sizeof(long long));
+    size_t o_cd = off; off += al(colt_d.size() * sizeof(double));
     size_t o_cnt = off; off += al(sizeof(unsigned long long));
     std::vector<char> host(off, 0);
     memcpy(&host[o_as], axis_sigma.data(), axis_sigma.size() * sizeof(int));
@@ -220,8 +228,9 @@ static csm_status build_tables(csm_geom_s* g) {
     memcpy(&host[o_wr], wrange.data(), wrange.size() * sizeof(int));
     memcpy(&host[o_rf], rowq_f.data(), rowq_f.size() * sizeof(float));
     memcpy(&host[o_rd], rowq_d.data(), rowq_d.size() * sizeof(double));
-    memcpy(&host[o_pfx], rowp_fx.data(), rowp_fx.size() * sizeof(long long));
-    memcpy(&host[o_pd], rowp_d.data(), rowp_d.size() * sizeof(double));
+    memcpy(&host[o_q4], rowq4.data(), rowq4.size() * sizeof(float));
+    memcpy(&host[o_cfx], colt_fx.data(), colt_fx.size() * sizeof(long long));
+    memcpy(&host[o_cd], colt_d.data(), colt_d.size() * sizeof(double));
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, off);
     if (e != cudaSuccess) { set_cuda_error(e); return e == cudaErrorMemoryAllocation ? CSM_ENOMEM : CSM_ECUDA; }
@@ -239,8 +248,9 @@ static csm_status build_tables(csm_geom_s* g) {
     g->t.wrange = (int*)(b + o_wr);
     g->t.rowq_f = (float*)(b + o_rf);
     g->t.rowq_d = (double*)(b + o_rd);
-    g->t.rowp_fx = (long long*)(b + o_pfx);
-    g->t.rowp_d = (double*)(b + o_pd);
+    g->t.rowq4 = (float4*)(b + o_q4);
+    g->t.colt_fx = (long long*)(b + o_cfx);
+    g->t.colt_d = (double*)(b + o_cd);
     g->t.counter = (unsigned long long*)(b + o_cnt);
     return CSM_OK;
 }
@@ -264,6 +274,8 @@ static csm_status finish_create(csm_geom_s* g, const double* angles, csm_geom_t*
         double tanb = std::max(fabs((-0.5 * g->nu) * g->du + g->u_off), fabs((0.5 * g->nu) * g->du + g->u_off)) / g->sdd;
         double uext = g->sdd * diag * (1.0 + tanb) / tmin;
         if (floor(uext / g->du) + 1.0 > (double)kMaxG) return CSM_EUNSUPPORTED;
+        // the kernels index one view's projections with 32-bit integers
+        if ((double)g->nv * g->nu >= 2147483647.0) return CSM_EUNSUPPORTED;
     }
     cudaError_t e = cudaGetDevice(&g->device);
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }

@@ -25,10 +25,11 @@ namespace csm {
 //   line_d      = the same two numbers in double
 //   inv2        = 1 / (2 |step|) per corner (float and double)
 //   wrange      = per element k: the walk cells [w0, w1) where its strip meets the grid
-//   rows (3D)   = per row corner l: q_l = v_l / sdd (float and double), and per view the
-//                 height of the plane { v(P) = v_l } = { z = q_l t(P) } above the grid's
-//                 bottom face at the centre of column (ix, iy), in units of c:
-//                     G_l(ix, iy) = A + ix B + iy C   (32.32 fixed point and double)
+//   rows (3D)   = per row corner l: q_l = v_l / sdd (float and double), and q_l as a float
+//                 pair hi + lo with 1/|q_l| (float4), from which the kernels form the height
+//                 of the plane { v(P) = v_l } = { z = q_l t(P) } at a column centre
+//   columns (3D) = per view the depth of column centres over c, T0 + ix Tx + iy Ty
+//                 (32.32 fixed point and double)
 // ---------------------------------------------------------------------------------------
 struct DeviceTables {
     int* axis_sigma = nullptr;     // [V][2]
@@ -41,8 +42,9 @@ struct DeviceTables {
     int* wrange = nullptr;         // [V][nu][2]
     float* rowq_f = nullptr;       // [nv+1]
     double* rowq_d = nullptr;      // [nv+1]
-    long long* rowp_fx = nullptr;  // [V][nv+1][3] row planes, 32.32 fixed point (3D)
-    double* rowp_d = nullptr;      // [V][nv+1][3]
+    float4* rowq4 = nullptr;       // [nv+1] {q hi, q lo, 1/|q|, 0}
+    long long* colt_fx = nullptr;  // [V][3] column-centre depth / c = T0 + ix Tx + iy Ty, 32.32 (3D)
+    double* colt_d = nullptr;      // [V][3]
     unsigned long long* counter = nullptr;  // scratch word for csm_nnz
 };
 
@@ -85,8 +87,9 @@ struct Geo {
     const int* wrange;
     const float* rowq_f;
     const double* rowq_d;
-    const long long* rowp_fx;
-    const double* rowp_d;
+    const float4* rowq4;
+    const long long* colt_fx;
+    const double* colt_d;
 };
 
 Geo make_geo(const csm_geom_s* g);

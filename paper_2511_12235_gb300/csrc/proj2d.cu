@@ -160,15 +160,17 @@ __device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict
 // ---------------------------------------------------------------------------------------
 // Forward, ray-driven: one thread per (view, element).  The thread walks the cells of its
 // fan strip along the view's walk axis; in each walked column it visits the cells between
-// its two corner lines and accumulates  W * x  for NB batch items.
+// its two corner lines and accumulates  W * x  for NB batch items.  A block holds 16
+// neighbouring elements of 4 neighbouring views: their strips cover nearly the same cells,
+// so a cell fetched into L1 for one view serves the others.
 // ---------------------------------------------------------------------------------------
 template <typename T, int NB>
 __global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0, const T* __restrict__ xs1,
                                                  void* __restrict__ p, int pdt, int B, int b_off, T scale,
                                                  int accumulate) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int v = blockIdx.y;
-    if (k >= g.nu) return;
+    const int k = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int v = blockIdx.y * 4 + (threadIdx.x >> 4);
+    if (k >= g.nu || v >= g.n_views) return;
     const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
     const int nc = axis == 0 ? g.ny : g.nx;
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
@@ -389,7 +391,7 @@ static csm_status run_forward(const csm_geom_s* gh, const void* x, void* p, int6
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 pb(32, 8), pg((gh->nx + 31) / 32, (gh->ny + 31) / 32);
         prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
-        dim3 fb(64), fg((gh->nu + 63) / 64, gh->n_views);
+        dim3 fb(64), fg((gh->nu + 15) / 16, (gh->n_views + 3) / 4);
         fwd2d_ray<T, NB><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
@@ -446,6 +448,7 @@ csm_status forward_2d(const csm_geom_s* g, const void* x, void* p, int64_t batch
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     if (flags & CSM_VOXEL_DRIVEN) return CSM_EUNSUPPORTED;
     if (!ws || ws_bytes < workspace_2d(g, 0, batch, dbl)) return CSM_EINVAL;
+    if ((g->n_views + 3) / 4 > 65535) return CSM_EUNSUPPORTED;
     return dbl ? fwd_nb<double>(g, x, p, batch, xdt, pdt, flags, ws, st)
                : fwd_nb<float>(g, x, p, batch, xdt, pdt, flags, ws, st);
 }

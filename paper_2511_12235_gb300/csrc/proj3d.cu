@@ -124,31 +124,40 @@ template <> struct G3<double> {
     static constexpr double eps = 1e-9;
 };
 
-// Row-plane height above the grid's bottom face at the centre of column (ix, iy), in units
-// of c; the local height above voxel iz's bottom face is (G - iz) c.
-struct RowF {
-    long long G;
-    __device__ __forceinline__ void at(const Geo& g, int v, int l, int ix, int iy) {
-        const long long* e = g.rowp_fx + 3 * ((size_t)v * (g.nv + 1) + l);
-        G = e[0] + (long long)ix * e[1] + (long long)iy * e[2];
-    }
-    __device__ __forceinline__ float rel(int iz) const {   // G - iz in float, exact integer part
-        int hi = (int)(G >> 32);
-        unsigned lo = (unsigned)(G & 0xffffffffull);
-        return (float)(hi - iz) + (float)lo * 2.3283064365386963e-10f;
-    }
-};
-struct RowD {
-    double G;
-    __device__ __forceinline__ void at(const Geo& g, int v, int l, int ix, int iy) {
-        const double* e = g.rowp_d + 3 * ((size_t)v * (g.nv + 1) + l);
-        G = e[0] + (double)ix * e[1] + (double)iy * e[2];
-    }
-    __device__ __forceinline__ double rel(int iz) const { return G - (double)iz; }
-};
-template <typename T> struct RowOf;
-template <> struct RowOf<float> { using type = RowF; };
-template <> struct RowOf<double> { using type = RowD; };
+// Depth of the centre of column (ix, iy) in view v over c, t_c / c = T0 + ix Tx + iy Ty
+// (per-view table).  FP32: summed in 32.32 fixed point (exact) and returned as the pair
+// integer part + fraction, both exact in float; FP64: in double.
+__device__ __forceinline__ void column_depth(const Geo& g, int v, int ix, int iy, float& hi, float& lo) {
+    const long long* e = g.colt_fx + 3 * v;
+    const long long t = e[0] + (long long)ix * e[1] + (long long)iy * e[2];
+    hi = (float)(int)(t >> 32);
+    lo = (float)(unsigned)(t & 0xffffffffll) * 2.3283064365386963e-10f;
+}
+__device__ __forceinline__ void column_depth(const Geo& g, int v, int ix, int iy, double& hi, double& lo) {
+    const double* e = g.colt_d + 3 * v;
+    hi = e[0] + (double)ix * e[1] + (double)iy * e[2];
+    lo = 0.0;
+}
+
+// Height of row corner plane l above the bottom face of voxel iz at the column centre, in
+// units of c:  h = q_l t_c / c - (iz - nz / 2)  (the plane is z = q_l t, the voxel's bottom
+// z0 + iz c).  FP32: the product of the float pairs q = qh + ql and t_c / c = dh + dl with
+// its rounding error recovered by an FMA, so h carries an absolute error of a few 1e-7
+// whatever the magnitudes of q t_c / c and iz.  Also returns q and 1/|q| (0 for q = 0).
+__device__ __forceinline__ float plane_height(const Geo& g, int l, int iz, float dh, float dl, float& q, float& iq) {
+    const float4 r = __ldg(g.rowq4 + l);
+    const float p = r.x * dh;
+    const float e = fmaf(r.x, dh, -p);
+    const float izp = (float)iz - 0.5f * (float)g.nz;
+    q = r.x;
+    iq = r.z;
+    return (p - izp) + (e + fmaf(r.x, dl, r.y * dh));
+}
+__device__ __forceinline__ double plane_height(const Geo& g, int l, int iz, double dh, double, double& q, double& iq) {
+    q = g.rowq_d[l];
+    iq = q != 0.0 ? 1.0 / fabs(q) : 0.0;
+    return q * dh - ((double)iz - 0.5 * (double)g.nz);
+}
 
 // ---------------------------------------------------------------------------------------
 // Layouts.  Forward reads x as xs0[ix][q][iz][iy][VW] (walk x) / xs1[iy][q][iz][ix][VW]
@@ -349,8 +358,10 @@ __device__ __forceinline__ T phi_p(const AtomP<T>& P, T g, T q, T iq, T c) {
 template <typename T>
 struct ColumnView {
     int ok, axis, sigma, k_first, ng;   // elements k_first .. k_first + ng (ng + 1 columns)
+    int kin;                            // all of them on the detector
     T tmin_w, tmax_w;                   // world depth range of the column
     T margin_c;                         // largest |t'| in the cell, in units of the voxel height c
+    T dh, dl;                           // centre depth / c as a pair (column_depth)
 };
 
 // Classification of the corner lines of one column's footprint, computed cooperatively by
@@ -382,6 +393,7 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
     }
     cv.tmin_w = tmin;
     cv.tmax_w = tmax;
+    column_depth(g, v, ix, iy, cv.dh, cv.dl);
     cv.margin_c = T(0.5) * (fabs(a * cs) + fabs(b * sn)) * G3<T>::ic(g);
     const T idu = G3<T>::idu(g);
     T f0 = floor((umin - G3<T>::u0(g)) * idu - G3<T>::eps), f1 = floor((umax - G3<T>::u0(g)) * idu + G3<T>::eps);
@@ -411,6 +423,7 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
     ng = ng > kMaxG ? kMaxG : ng;          // excluded by the geometry check
     cv.ng = ng;
     cv.k_first = ga - 1;
+    cv.kin = cv.k_first >= 0 && cv.k_first + ng < g.nu;
     cv.ok = 1;
 }
 
@@ -480,7 +493,6 @@ __device__ __forceinline__ bool voxel_rows(const Geo& g, T z0w, T z1w, T tmin, T
 template <typename T, typename Emit>
 __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int iy, int iz, const ColumnView<T>& cv,
                                               const AtomP<T>* atoms, const AtomP<T>& full, T* scratch, Emit&& emit) {
-    using R = typename RowOf<T>::type;
     const T c = G3<T>::c(g);
     const T z0w = G3<T>::z0(g) + iz * c;
     int l0, l1;
@@ -492,13 +504,11 @@ __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int i
 #pragma unroll 1
     for (int r = l0; r <= l1 + 1; ++r) {
         const int cur = r & 1, prv = cur ^ 1;
-        R row;
-        row.at(g, v, r, ix, iy);
-        const T h = row.rel(iz);                 // plane height above the voxel bottom, units of c
-        const T q = G3<T>::q(g, r);
+        T q, iq;
+        const T h = plane_height(g, r, iz, cv.dh, cv.dl, q, iq);   // above the voxel bottom, units of c
         const T m = fabs(q) * cv.margin_c;       // height change across the cell, units of c
         const int cls = h + m <= T(0) ? 0 : (h - m >= T(1) ? 2 : 1);   // below / above / crossing
-        const T gw = h * c, iq = q != T(0) ? G3<T>::div(T(1), fabs(q)) : T(0);
+        const T gw = h * c;
 #pragma unroll 1
         for (int j = 0; j < na; ++j) {
             const AtomP<T>& P = j == 0 ? full : atoms[j - 1];
@@ -515,7 +525,7 @@ __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int i
             const T S = j < ng ? PHI(cur, j + 1) - PHI(prv, j + 1) : (cv.sigma > 0 ? sf : T(0));
             const int k = cv.k_first + j;
             const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
-            if (k >= 0 && k < g.nu && wt != T(0)) emit(k, l, wt);
+            if ((cv.kin || (k >= 0 && k < g.nu)) && wt != T(0)) emit(k, l, wt);
             prevS = S;
         }
     }
@@ -567,7 +577,7 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
 #pragma unroll
             for (int i = 0; i < NB; ++i) sum[i] = T(0);
             voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, [&](int k, int l, T wt) {
-                fma_vec<T, NB>(sum, wt, pv + ((size_t)l * g.nu + k) * NB);
+                fma_vec<T, NB>(sum, wt, pv + (size_t)(l * g.nu + k) * NB);
             });
 #pragma unroll
             for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sum[i];
@@ -603,7 +613,6 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
     __shared__ AtomP<T> atoms_s[FW][3];   // line k, line k+1, whole cell
     __shared__ T rows_s[FW][RWMAX * NB];
     using L = typename LineOf<T>::type;
-    using R = typename RowOf<T>::type;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int k = blockIdx.x * FW + wid;
     const int v = blockIdx.y;
@@ -641,10 +650,10 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
             const bool fa = a0 >= T(1) && a1 >= T(1), fb = b0 >= T(1) && b1 >= T(1);
             if ((ea && eb) || (fa && fb)) continue;        // the strip misses this cell (warp-uniform)
             const int ix = axis == 0 ? w : cc, iy = axis == 0 ? cc : w;
-            R rl, rh;
-            rl.at(g, v, L0, ix, iy);
-            rh.at(g, v, L0 + nrow, ix, iy);
-            const T zlo = floor(rl.rel(0) - mz), zhi = floor(rh.rel(0) + mz);
+            T dh, dl, qq, iqq;
+            column_depth(g, v, ix, iy, dh, dl);
+            const T zlo = floor(plane_height(g, L0, 0, dh, dl, qq, iqq) - mz);
+            const T zhi = floor(plane_height(g, L0 + nrow, 0, dh, dl, qq, iqq) + mz);
             if (zhi < T(0) || zlo > T(g.nz - 1)) continue;
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
@@ -700,10 +709,8 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                 // Phi of both lines at corners l0 .. l1+1; entries of rows in the window
                 T pa = T(0), pb = T(0);
                 for (int r = l0; r <= l1 + 1; ++r) {
-                    R row;
-                    row.at(g, v, r, ix, iy);
-                    const T h = row.rel(iz);
-                    const T q = G3<T>::q(g, r);
+                    T q, iq;
+                    const T h = plane_height(g, r, iz, dh, dl, q, iq);
                     const T m = fabs(q) * margin_c;
                     T ca, cb;
                     if (h + m <= T(0)) {
@@ -713,7 +720,7 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                         ca = ea ? T(0) : c * Pa.A;
                         cb = eb ? T(0) : c * Pb.A;
                     } else {
-                        const T gw = h * c, iq = q != T(0) ? G3<T>::div(T(1), fabs(q)) : T(0);
+                        const T gw = h * c;
                         ca = ea ? T(0) : phi_p<T>(Pa, gw, q, iq, c);
                         cb = eb ? T(0) : phi_p<T>(Pb, gw, q, iq, c);
                     }
