@@ -140,6 +140,36 @@ def measured_peaks():
         return {}
 
 
+def kernel_source_hash() -> str:
+    """sha256 over the CUDA sources and the C header (names and bytes, sorted by name)."""
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2511_12235_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
+    files.append(os.path.join(ROOT, "include", "csm.h"))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def dram_traffic(workload: str, kernel: str):
+    """DRAM bytes (read + write) per launch of `kernel` ("forward" / "back") on `workload`
+    from the committed ncu capture (profiles/dram_traffic.json), or None when there is none
+    or the kernel sources changed since it was taken."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("source_sha256") != kernel_source_hash():
+        return None
+    v = d.get(workload, {}).get(kernel)
+    return float(v) if v is not None else None
+
+
 def fp32_alu_peak_tflops(sm_mhz: float) -> float:
     """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -317,7 +347,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": 4 * args.steps,
         "kernels_ms": {"forward": t_fwd, "back": t_back},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": dram_traffic(wl, dom),
+                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                      "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x %.0f MHz (max SM clock); "
                                   "algorithmic flops = nnz x (%d + 2 x batch)" % (sm_max, fpe)},
         "clocks": clk,
