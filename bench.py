@@ -255,6 +255,7 @@ def run_ours(args, rank, world, local):
         xs_host = np.stack([synth.ellipse_phantom(g["nx"], s) for s in seeds]).astype(np.float32)
     else:
         xs_host = np.stack([synth.ellipsoid_phantom(g["nx"], s, dtype=np.float32) for s in seeds])
+    x_zero_fraction = float((xs_host == 0).mean())
     x = torch.from_numpy(xs_host).to(dev).to(tdt)
     P = csm.Projector(g, device=dev)
     nnz = P.nnz()
@@ -341,7 +342,7 @@ def run_ours(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": sdt, "data": "synthetic",
         "config": {"workload": wl, "grid": [g["nx"], g["ny"]] + ([g["nz"]] if g["dim"] == 3 else []),
                    "views": g["n_views"], "detector": [g["nu"]] + ([g["nv"]] if g["dim"] == 3 else []),
-                   "batch": batch, "nnz_per_item": nnz,
+                   "batch": batch, "nnz_per_item": nnz, "x_zero_fraction": round(x_zero_fraction, 4),
                    "l2": "flushed before every timed step (512 MiB write, untimed)",
                    "step": "forward over all views + back projection of the batch"},
         "gpu_launches": 4 * args.steps,

@@ -16,7 +16,9 @@ Workloads (the paper's datasets are not used; every input is synthetic):
                   source-detector 1500.
 
 Views are phi_v = 2 pi v / N_p, v = 0..N_p-1 (the paper's "equidistant in [0, 2pi)").
-Phantoms are sums of random ellipses (ellipsoids) evaluated at pixel (voxel) centres.
+Phantoms are a large "body" ellipse (ellipsoid) around the centre plus random inner
+ellipses (ellipsoids), evaluated at pixel (voxel) centres: like a scanned object, most of
+the field of view is nonzero and the grid's corners are air.
 """
 from __future__ import annotations
 
@@ -80,12 +82,23 @@ def config(name: str) -> dict:
     return CONFIGS[name]()
 
 
-def ellipse_phantom(n: int, seed: int, n_ellipses: int = 10, ny: int | None = None) -> np.ndarray:
-    """Sum of ``n_ellipses`` random ellipses on an n x ny grid of unit pixels centred at 0.
+def _body_and_inner(rng, n_inner):
+    """Draws (centre offset, semi-axes, value) triples in units of the half-width R: first the
+    body (centre within 0.05, semi-axes U[0.75, 0.92], value U[0.1, 0.3]), then the inner
+    shapes (centre within 0.7, semi-axes U[0.05, 0.35], value U[0, 1])."""
+    out = [("body", 0.05, (0.75, 0.92), (0.1, 0.3))]
+    out += [("inner", 0.7, (0.05, 0.35), (0.0, 1.0))] * n_inner
+    return out
 
-    Centre uniform in the disc of radius 0.7 * n/2; semi-axes U[0.05, 0.35] * n/2;
-    orientation U[0, pi); value U[0, 1].  A pixel takes the sum of the values of the
-    ellipses that contain its centre.  Returns float64 [ny][n].
+
+def ellipse_phantom(n: int, seed: int, n_ellipses: int = 10, ny: int | None = None) -> np.ndarray:
+    """A body ellipse and ``n_ellipses`` random ellipses on an n x ny grid of unit pixels
+    centred at 0 (R = half the smaller side).
+
+    Body: centre uniform in the disc of radius 0.05 R, semi-axes U[0.75, 0.92] R, value
+    U[0.1, 0.3].  Inner ellipses: centre uniform in the disc of radius 0.7 R, semi-axes
+    U[0.05, 0.35] R, value U[0, 1].  Orientation U[0, pi).  A pixel takes the sum of the
+    values of the ellipses that contain its centre.  Returns float64 [ny][n].
     """
     ny = n if ny is None else ny
     rng = np.random.default_rng(seed)
@@ -94,13 +107,13 @@ def ellipse_phantom(n: int, seed: int, n_ellipses: int = 10, ny: int | None = No
     X, Y = np.meshgrid(xs, ys)
     R = 0.5 * min(n, ny)
     img = np.zeros((ny, n), dtype=np.float64)
-    for _ in range(n_ellipses):
-        r = 0.7 * R * math.sqrt(rng.uniform())
+    for _, rc, (a0, a1), (v0, v1) in _body_and_inner(rng, n_ellipses):
+        r = rc * R * math.sqrt(rng.uniform())
         th = rng.uniform(0, 2 * math.pi)
         cx, cy = r * math.cos(th), r * math.sin(th)
-        ax, ay = rng.uniform(0.05, 0.35, size=2) * R
+        ax, ay = rng.uniform(a0, a1, size=2) * R
         ang = rng.uniform(0, math.pi)
-        val = rng.uniform(0, 1)
+        val = rng.uniform(v0, v1)
         ca, sa = math.cos(ang), math.sin(ang)
         dx, dy = X - cx, Y - cy
         xr = dx * ca + dy * sa
@@ -120,26 +133,34 @@ def _random_rotation(rng) -> np.ndarray:
     ])
 
 
-def ellipsoid_phantom(n: int, seed: int, n_ellipsoids: int = 10, dtype=np.float64,
-                      slab: int = 32) -> np.ndarray:
-    """Sum of random ellipsoids on an n^3 grid of unit voxels centred at 0 ([nz][ny][nx]).
-
-    Centre uniform in the ball of radius 0.7 * n/2, semi-axes U[0.05, 0.35] * n/2, a
-    uniformly random rotation, value U[0, 1].  Evaluated slab by slab to bound memory.
-    """
+def _ellipsoid_params(n: int, seed: int, n_ellipsoids: int):
     rng = np.random.default_rng(seed)
     R = 0.5 * n
     params = []
-    for _ in range(n_ellipsoids):
+    for _, rc, (a0, a1), (v0, v1) in _body_and_inner(rng, n_ellipsoids):
         d = rng.normal(size=3)
         d /= np.linalg.norm(d)
-        c = d * 0.7 * R * rng.uniform() ** (1.0 / 3.0)
-        ax = rng.uniform(0.05, 0.35, size=3) * R
+        c = d * rc * R * rng.uniform() ** (1.0 / 3.0)
+        ax = rng.uniform(a0, a1, size=3) * R
         Rm = _random_rotation(rng)
-        val = rng.uniform(0, 1)
+        val = rng.uniform(v0, v1)
         params.append((c, ax, Rm, val))
-    out = np.zeros((n, n, n), dtype=dtype)
+    return params
+
+
+def ellipsoid_phantom(n: int, seed: int, n_ellipsoids: int = 10, dtype=np.float64,
+                      slab: int = 32) -> np.ndarray:
+    """A body ellipsoid and ``n_ellipsoids`` random ellipsoids on an n^3 grid of unit voxels
+    centred at 0 ([nz][ny][nx]; R = n/2).
+
+    Body: centre uniform in the ball of radius 0.05 R, semi-axes U[0.75, 0.92] R, value
+    U[0.1, 0.3].  Inner ellipsoids: centre uniform in the ball of radius 0.7 R, semi-axes
+    U[0.05, 0.35] R, value U[0, 1].  Uniformly random rotations.  Evaluated slab by slab to
+    bound memory.
+    """
+    params = _ellipsoid_params(n, seed, n_ellipsoids)
     xs = (np.arange(n) - n / 2.0 + 0.5)
+    out = np.zeros((n, n, n), dtype=dtype)
     Y, X = np.meshgrid(xs, xs, indexing="ij")
     for z0 in range(0, n, slab):
         zs = xs[z0:z0 + slab]
@@ -160,18 +181,10 @@ def ellipsoid_phantom_torch(n: int, seed: int, device, n_ellipsoids: int = 10):
     """The same phantom as ``ellipsoid_phantom`` (same parameter draws), evaluated with torch
     on ``device`` (float32), for large serving requests."""
     import torch
-    rng = np.random.default_rng(seed)
-    R = 0.5 * n
     xs = torch.arange(n, device=device, dtype=torch.float32) - n / 2.0 + 0.5
     Z, Y, X = torch.meshgrid(xs, xs, xs, indexing="ij")
     out = torch.zeros((n, n, n), device=device, dtype=torch.float32)
-    for _ in range(n_ellipsoids):
-        d = rng.normal(size=3)
-        d /= np.linalg.norm(d)
-        c = d * 0.7 * R * rng.uniform() ** (1.0 / 3.0)
-        ax = rng.uniform(0.05, 0.35, size=3) * R
-        Rm = _random_rotation(rng)
-        val = rng.uniform(0, 1)
+    for c, ax, Rm, val in _ellipsoid_params(n, seed, n_ellipsoids):
         dx, dy, dz = X - float(c[0]), Y - float(c[1]), Z - float(c[2])
         q = torch.zeros_like(out)
         for r in range(3):
