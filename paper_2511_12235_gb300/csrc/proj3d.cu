@@ -369,9 +369,13 @@ struct ColumnView {
 // projected by lane groups of four, the lines k0 .. k1+1 of the footprint are classified one
 // per lane, and ballots give the first and last line that is not of the "before" / "after"
 // type.  Elements k_first .. k_first + ng carry weight, the crossing lines are
-// k_first + 1 .. k_first + ng.
+// k_first + 1 .. k_first + ng.  With [klo, khi] only those lines are classified (lines below
+// the footprint count as "before", lines above it as "after"): the entries of the elements
+// klo .. khi-1 are then exact, the others must not be used.  cv.ok = 0 when the cell gives
+// those elements no weight.
 template <typename T>
-__device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy, int lane, ColumnView<T>& cv) {
+__device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy, int lane, ColumnView<T>& cv,
+                                            int klo = 0, int khi = 0x7fffffff) {
     using L = typename LineOf<T>::type;
     const T a = G3<T>::a(g), b = G3<T>::b(g);
     const T X0 = G3<T>::x0(g) + ix * a, Y0 = G3<T>::y0(g) + iy * b;
@@ -400,15 +404,17 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
     cv.ok = 0;
     if (f1 < T(0) || f0 > T(g.nu - 1)) return;
     const int k0 = f0 < T(0) ? 0 : (int)f0, k1 = f1 > T(g.nu - 1) ? g.nu - 1 : (int)f1;
+    const int la = k0 > klo ? k0 : klo, lb = k1 + 1 < khi ? k1 + 1 : khi;   // lines classified
+    if (la > lb) return;
     const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
     cv.axis = axis;
     cv.sigma = sigma;
     const int w = axis == 0 ? ix : iy, cc = axis == 0 ? iy : ix;
-    // line k0 + lane; "before" type: empty for sigma > 0, whole cell for sigma < 0
+    // line la + lane; "before" type: empty for sigma > 0, whole cell for sigma < 0
     bool not_before = false, not_after = false;
-    if (lane <= k1 + 1 - k0) {
+    if (lane <= lb - la) {
         L line;
-        line.load(g, v, k0 + lane, w);
+        line.load(g, v, la + lane, w);
         T y0, y1;
         line.offsets(cc, y0, y1);
         const bool empty = y0 <= T(0) && y1 <= T(0), full = y0 >= T(1) && y1 >= T(1);
@@ -416,8 +422,8 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
         not_after = !(sigma > 0 ? full : empty);
     }
     const unsigned mb = __ballot_sync(0xffffffffu, not_before), ma = __ballot_sync(0xffffffffu, not_after);
-    const int ga = mb ? k0 + __ffs(mb) - 1 : k1 + 2;     // every line is of the "before" type
-    int gb = ma ? k0 + 31 - __clz(ma) : k0 - 1;          // every line is of the "after" type
+    const int ga = mb ? la + __ffs(mb) - 1 : lb + 1;     // every line is of the "before" type
+    int gb = ma ? la + 31 - __clz(ma) : la - 1;          // every line is of the "after" type
     if (gb < ga - 1) gb = ga - 1;
     int ng = gb - ga + 1;
     ng = ng > kMaxG ? kMaxG : ng;          // excluded by the geometry check
@@ -486,13 +492,14 @@ __device__ __forceinline__ bool voxel_rows(const Geo& g, T z0w, T z1w, T tmin, T
     return l0 <= l1;
 }
 
-// Visits every nonzero W(k, l) of voxel iz in the column (ix, iy) for view v:
-// emit(k, l, W).  atoms: the column-view's crossing-line atoms; full: the whole-cell atom;
-// scratch: this lane's 2 (kMaxG + 1) slots, 32 elements apart (one per lane of the warp), for
-// Phi per atom on two consecutive row corner planes.
-template <typename T, typename Emit>
+// Visits every nonzero W(k, l) of voxel iz in the column (ix, iy) for view v through a sink:
+// sink.add(k, l, W) for each entry.  atoms: the column-view's
+// crossing-line atoms; full: the whole-cell atom; scratch: this lane's 2 (kMaxG + 1) slots,
+// 32 elements apart (one per lane of the warp), for Phi per atom on two consecutive row
+// corner planes.
+template <typename T, typename Sink>
 __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int iy, int iz, const ColumnView<T>& cv,
-                                              const AtomP<T>* atoms, const AtomP<T>& full, T* scratch, Emit&& emit) {
+                                              const AtomP<T>* atoms, const AtomP<T>& full, T* scratch, Sink& sink) {
     const T c = G3<T>::c(g);
     const T z0w = G3<T>::z0(g) + iz * c;
     int l0, l1;
@@ -525,12 +532,23 @@ __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int i
             const T S = j < ng ? PHI(cur, j + 1) - PHI(prv, j + 1) : (cv.sigma > 0 ? sf : T(0));
             const int k = cv.k_first + j;
             const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
-            if ((cv.kin || (k >= 0 && k < g.nu)) && wt != T(0)) emit(k, l, wt);
+            if ((cv.kin || (k >= 0 && k < g.nu)) && wt != T(0)) sink.add(k, l, wt);
             prevS = S;
         }
     }
 #undef PHI
 }
+
+// Sink of the back projection: W p gathered from this view's projections.
+template <typename T, int NB>
+struct GatherSink {
+    const T* pv;        // this view's projections, [nv][nu][NB]
+    int nu;
+    T sum[NB];
+    __device__ __forceinline__ void add(int k, int l, T wt) {
+        fma_vec<T, NB>(sum, wt, pv + (size_t)(l * nu + k) * NB);
+    }
+};
 
 // ---------------------------------------------------------------------------------------
 // Back projection: one warp per voxel column and window of ZW voxels in z (ZW = 64, 128 or
@@ -571,16 +589,15 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
         __syncwarp();
         column_atoms<T>(g, v, ix, iy, cv, lane, atoms);
         __syncwarp();
-        const T* pv = ps + (size_t)v * g.nv * g.nu * NB;
+        GatherSink<T, NB> sink;
+        sink.pv = ps + (size_t)v * g.nv * g.nu * NB;
+        sink.nu = g.nu;
         for (int iz = z0 + lane; iz <= z1; iz += 32) {
-            T sum[NB];
 #pragma unroll
-            for (int i = 0; i < NB; ++i) sum[i] = T(0);
-            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, [&](int k, int l, T wt) {
-                fma_vec<T, NB>(sum, wt, pv + (size_t)(l * g.nu + k) * NB);
-            });
+            for (int i = 0; i < NB; ++i) sink.sum[i] = T(0);
+            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, sink);
 #pragma unroll
-            for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sum[i];
+            for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sink.sum[i];
         }
     }
     __syncwarp();
@@ -596,46 +613,81 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
 }
 
 // ---------------------------------------------------------------------------------------
-// Forward projection, ray-driven with row windows: one warp per (view, detector column k,
-// window of RW consecutive rows).  The warp walks the top-view strip of column k cell by
-// cell (as in 2D); per cell two lanes build the atoms of the strip's corner lines, then the
-// lanes take the voxels of the column that the window's rows reach (one voxel per lane,
-// 32 at a time), form their entries for column k and add W x into per-row sums in shared
-// memory, which the warp writes to p at the end (each element written by exactly one warp).
+// Forward projection, ray-driven over element groups: one warp per (view, group of KW
+// neighbouring detector columns kg .. kg+KW-1, window of rw consecutive rows).  The warp
+// walks the union of the group's top-view strips cell by cell (as in 2D); per cell it
+// classifies the group's KW + 1 corner lines (column_view restricted to them), builds the
+// tables of the crossing ones (one (line, piece) per lane; the whole-cell table is built once
+// per warp), then the lanes take the voxels of the column that the window's rows reach (one
+// voxel per lane, 32 at a time), form their entries with the back projection's voxel_entries
+// and add W x into per-(column, row) sums in shared memory, which the warp writes to p at the
+// end (each element written by exactly one warp).  A line's table serves the two columns it
+// bounds, so the group shares them; cells whose voxels in reach are all zero are skipped
+// before any table is built.  The window is as tall as a shared-memory budget allows (384
+// rows for one FP32 batch item).
 // ---------------------------------------------------------------------------------------
-constexpr int FW = 4;       // warps per block
-constexpr int RWMAX = 96;   // rows per warp (upper bound of the window)
+constexpr int FW = 4;                // warps per block
+constexpr int KW = 4;                // detector columns per warp
+
+// Sink of the forward projection: W x added to the (column, row) sums of the warp's group.
+template <typename T, int NB>
+struct RowSink {
+    T* rows;
+    int rw, kg, nk, L0, nrow;
+    T xv[NB];
+    __device__ __forceinline__ void add(int k, int l, T wt) {
+        const int kk = k - kg, ll = l - L0;
+        if (kk >= 0 && kk < nk && ll >= 0 && ll < nrow) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) atomicAdd(&rows[(kk * rw + ll) * NB + i], wt * xv[i]);
+        }
+    }
+};
+constexpr int FWD_SMEM = 24 * 1024;  // shared-memory budget of one block's row sums (6 blocks / SM)
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __restrict__ xs0, const T* __restrict__ xs1,
-                                                    void* __restrict__ p, int pdt, int B, int b_off, T scale,
-                                                    int accumulate) {
-    __shared__ AtomP<T> atoms_s[FW][3];   // line k, line k+1, whole cell
-    __shared__ T rows_s[FW][RWMAX * NB];
+__global__ void __launch_bounds__(32 * FW, 6) fwd3d_grp(Geo g, int rw, const T* __restrict__ xs0,
+                                                     const T* __restrict__ xs1, void* __restrict__ p, int pdt,
+                                                     int B, int b_off, T scale, int accumulate) {
+    __shared__ AtomP<T> atoms_s[FW][kMaxG + 1];
+    __shared__ T scratch_s[FW][2 * (kMaxG + 1) * 32];
+    extern __shared__ __align__(16) unsigned char fwd_dyn[];   // [FW][KW][rw][NB] sums
     using L = typename LineOf<T>::type;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int k = blockIdx.x * FW + wid;
+    const int kg = (blockIdx.x * FW + wid) * KW;
     const int v = blockIdx.y;
     const int L0 = blockIdx.z * rw;
-    if (k >= g.nu || L0 >= g.nv) return;                  // whole warp leaves together
-    const int nrow = min(rw, g.nv - L0);
-    T* rows = rows_s[wid];
-    for (int i = lane; i < nrow * NB; i += 32) rows[i] = T(0);
-    const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+    if (kg >= g.nu || L0 >= g.nv) return;                 // whole warp leaves together
+    const int nk = min(KW, g.nu - kg), nrow = min(rw, g.nv - L0);
+    T* rows = reinterpret_cast<T*>(fwd_dyn) + (size_t)wid * KW * rw * NB;   // [(k - kg) * rw + row][NB]
+    for (int i = lane; i < KW * rw * NB; i += 32) rows[i] = T(0);
+    AtomP<T>* atoms = atoms_s[wid];
+    T* scratch = scratch_s[wid] + lane;
+    const int axis = g.axis_sigma[2 * v];
     const int nc = axis == 0 ? g.ny : g.nx;
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
     const T a = G3<T>::a(g), b = G3<T>::b(g), c = G3<T>::c(g);
     const T hw = axis == 0 ? a : b, hc = axis == 0 ? b : a;
-    const T cs = G3<T>::cs(g, v, 0), sn = G3<T>::cs(g, v, 1), s = G3<T>::s(g);
+    const T cs = G3<T>::cs(g, v, 0), sn = G3<T>::cs(g, v, 1);
     const T margin_c = T(0.5) * (fabs(a * cs) + fabs(b * sn)) * G3<T>::ic(g);   // units of c
     const T q_lo = G3<T>::q(g, L0), q_hi = G3<T>::q(g, L0 + nrow);
     const T mz = (fabs(q_lo) > fabs(q_hi) ? fabs(q_lo) : fabs(q_hi)) * margin_c + T(1e-3);
-    const int w0 = g.wrange[2 * ((size_t)v * g.nu + k)], w1 = g.wrange[2 * ((size_t)v * g.nu + k) + 1];
+    // walk range: the union of the group's elements' ranges
+    int w0 = 0x7fffffff, w1 = -1;
+    if (lane < nk) {
+        w0 = g.wrange[2 * ((size_t)v * g.nu + kg + lane)];
+        w1 = g.wrange[2 * ((size_t)v * g.nu + kg + lane) + 1];
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        w0 = min(w0, __shfl_xor_sync(0xffffffffu, w0, o));
+        w1 = max(w1, __shfl_xor_sync(0xffffffffu, w1, o));
+    }
     L la, lb;
-    la.load(g, v, k, w0);
-    lb.load(g, v, k + 1, w0);
-    // the whole-cell atom is the same in every cell of the view: built once
-    if (lane < 5) build_piece<T>(atoms_s[wid][2], lane + 1, T(2), T(2), hw, hc, axis, cs, sn);
+    la.load(g, v, kg, w0);
+    lb.load(g, v, kg + nk, w0);
+    // the whole-cell table is the same in every cell of the view: built once
+    if (lane < 5) build_piece<T>(atoms[kMaxG], lane + 1, T(2), T(2), hw, hc, axis, cs, sn);
     __syncwarp();
     for (int w = w0; w < w1; ++w) {
         int clo = min(la.cell_lo(), lb.cell_lo());
@@ -643,22 +695,19 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
         clo = max(clo, 0);
         chi = min(chi, nc - 1);
         for (int cc = clo; cc <= chi; ++cc) {
-            T a0, a1, b0, b1;
-            la.offsets(cc, a0, a1);
-            lb.offsets(cc, b0, b1);
-            const bool ea = a0 <= T(0) && a1 <= T(0), eb = b0 <= T(0) && b1 <= T(0);
-            const bool fa = a0 >= T(1) && a1 >= T(1), fb = b0 >= T(1) && b1 >= T(1);
-            if ((ea && eb) || (fa && fb)) continue;        // the strip misses this cell (warp-uniform)
             const int ix = axis == 0 ? w : cc, iy = axis == 0 ? cc : w;
-            T dh, dl, qq, iqq;
-            column_depth(g, v, ix, iy, dh, dl);
-            const T zlo = floor(plane_height(g, L0, 0, dh, dl, qq, iqq) - mz);
-            const T zhi = floor(plane_height(g, L0 + nrow, 0, dh, dl, qq, iqq) + mz);
+            ColumnView<T> cv;
+            column_view<T>(g, v, ix, iy, lane, cv, kg, kg + nk);
+            if (!cv.ok) continue;                          // warp-uniform
+            // voxels of the column that the window's rows reach
+            T qq, iqq;
+            const T zlo = floor(plane_height(g, L0, 0, cv.dh, cv.dl, qq, iqq) - mz);
+            const T zhi = floor(plane_height(g, L0 + nrow, 0, cv.dh, cv.dl, qq, iqq) + mz);
             if (zhi < T(0) || zlo > T(g.nz - 1)) continue;
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
             const T* xcol = xs + ((size_t)w * g.nz) * nc * NB + (size_t)cc * NB;
-            // cells whose voxels in reach are all zero add nothing: skip them before any atom
+            // cells whose voxels in reach are all zero add nothing: skip them before any table
             // is built
             bool nzv = false;
             for (int zb = izlo; zb <= izhi && !__any_sync(0xffffffffu, nzv); zb += 32) {
@@ -669,27 +718,12 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                 }
             }
             if (!__any_sync(0xffffffffu, nzv)) continue;
-            // atoms of the crossing lines (a line above the cell uses the whole-cell atom)
             __syncwarp();
-            if (lane < 10) {                                // (line, piece) per lane
-                const int j = lane >= 5 ? 1 : 0, pc = lane - 5 * j + 1;
-                if (j ? !(eb || fb) : !(ea || fa))
-                    build_piece<T>(atoms_s[wid][j], pc, j ? b0 : a0, j ? b1 : a1, hw, hc, axis, cs, sn);
+            for (int it = lane; it < cv.ng * 5; it += 32) {
+                const int i = it / 5;
+                column_piece<T>(g, v, ix, iy, cv, i, it - 5 * i + 1, atoms[i]);
             }
             __syncwarp();
-            const AtomP<T>& Pa = atoms_s[wid][fa ? 2 : 0];
-            const AtomP<T>& Pb = atoms_s[wid][fb ? 2 : 1];
-            // depth range of the column (the same for all its voxels)
-            T tmin = T(1e30), tmax = T(-1e30);
-            {
-                const T X0 = G3<T>::x0(g) + ix * a, Y0 = G3<T>::y0(g) + iy * b;
-#pragma unroll
-                for (int qq = 0; qq < 4; ++qq) {
-                    const T t = s - (X0 + ((qq & 1) ? a : T(0))) * cs - (Y0 + ((qq & 2) ? b : T(0))) * sn;
-                    tmin = t < tmin ? t : tmin;
-                    tmax = t > tmax ? t : tmax;
-                }
-            }
             for (int zb = izlo; zb <= izhi; zb += 32) {
                 const int iz = zb + lane;
                 if (iz > izhi) continue;
@@ -701,62 +735,36 @@ __global__ void __launch_bounds__(32 * FW) fwd3d_rw(Geo g, int rw, const T* __re
                     any |= xv[i] != T(0);
                 }
                 if (!any) continue;
-                // rows of this voxel at this cell, clipped to the window
-                const T z0w = G3<T>::z0(g) + iz * c;
-                int l0, l1;
-                if (!voxel_rows<T>(g, z0w, z0w + c, tmin, tmax, l0, l1)) continue;
-                if (l1 < L0 || l0 >= L0 + nrow) continue;
-                // Phi of both lines at corners l0 .. l1+1; entries of rows in the window
-                T pa = T(0), pb = T(0);
-                for (int r = l0; r <= l1 + 1; ++r) {
-                    T q, iq;
-                    const T h = plane_height(g, r, iz, dh, dl, q, iq);
-                    const T m = fabs(q) * margin_c;
-                    T ca, cb;
-                    if (h + m <= T(0)) {
-                        ca = T(0);
-                        cb = T(0);
-                    } else if (h - m >= T(1)) {
-                        ca = ea ? T(0) : c * Pa.A;
-                        cb = eb ? T(0) : c * Pb.A;
-                    } else {
-                        const T gw = h * c;
-                        ca = ea ? T(0) : phi_p<T>(Pa, gw, q, iq, c);
-                        cb = eb ? T(0) : phi_p<T>(Pb, gw, q, iq, c);
-                    }
-                    if (r > l0) {
-                        const int l = r - 1;
-                        if (l >= L0 && l < L0 + nrow) {
-                            T wt = (cb - pb) - (ca - pa);
-                            wt = sigma > 0 ? wt : -wt;
-                            if (wt != T(0)) {
+                RowSink<T, NB> sink{rows, rw, kg, nk, L0, nrow};
 #pragma unroll
-                                for (int i = 0; i < NB; ++i) atomicAdd(&rows[(l - L0) * NB + i], wt * xv[i]);
-                            }
-                        }
-                    }
-                    pa = ca;
-                    pb = cb;
-                }
+                for (int i = 0; i < NB; ++i) sink.xv[i] = xv[i];
+                voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, sink);
             }
         }
         la.step();
         lb.step();
     }
     __syncwarp();
-    for (int j = lane; j < nrow; j += 32) {
+    for (int idx = lane; idx < nk * nrow; idx += 32) {
+        const int j = idx / nk, kk = idx - j * nk;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
             const int bidx = b_off + i;
             if (bidx < B)
-                store_any3<T>(p, (((size_t)bidx * g.n_views + v) * g.nv + L0 + j) * g.nu + k, pdt,
-                              rows[j * NB + i] * scale, accumulate != 0);
+                store_any3<T>(p, (((size_t)bidx * g.n_views + v) * g.nv + L0 + j) * g.nu + kg + kk, pdt,
+                              rows[(kk * rw + j) * NB + i] * scale, accumulate != 0);
         }
     }
 }
 
 // Number of (voxel, view, element) whose volume exceeds 1e-6 of the voxel's (column-warps as
 // in the back projection).
+struct CountSink {
+    float thr;
+    unsigned long long n;
+    __device__ __forceinline__ void add(int, int, float wt) { n += fabsf(wt) > thr; }
+};
+
 __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long long* counter) {
     __shared__ AtomP<float> atoms_s[BW][kMaxG + 1];
     __shared__ float scratch_s[BW][2 * (kMaxG + 1) * 32];
@@ -781,9 +789,10 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
         __syncwarp();
         column_atoms<float>(g, v, ix, iy, cv, lane, atoms);
         __syncwarp();
+        CountSink sink{thr, 0ull};
         for (int iz = z0 + lane; iz <= z1; iz += 32)
-            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch,
-                                 [&](int, int, float wt) { cnt += fabsf(wt) > thr; });
+            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, sink);
+        cnt += sink.n;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
     if (lane == 0 && cnt) atomicAdd(counter, cnt);
@@ -792,13 +801,11 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
 // ---------------------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------------------
-// Rows per forward warp: the voxels those rows reach in one cell (at the largest depth) fit
-// in two passes of 32 lanes.
-static int rows_per_warp(const csm_geom_s* g) {
-    const double r = sqrt(pow(0.5 * g->nx * g->a, 2) + pow(0.5 * g->ny * g->b, 2));
-    const double tmax = g->s + r;
-    int rw = (int)floor(60.0 * g->sdd * g->c / (tmax * g->dv));
-    return std::max(8, std::min(RWMAX, rw));
+// Rows per forward warp: all of them when the block's row sums fit the shared-memory budget,
+// else the largest window that does (at least 32 rows).
+static int rows_per_warp(const csm_geom_s* g, int nb, size_t elem) {
+    const int cap = (int)(FWD_SMEM / ((size_t)FW * KW * nb * elem));
+    return std::max(32, std::min(g->nv, cap));
 }
 
 template <typename T, int NB>
@@ -811,13 +818,18 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
     T* xs0 = (T*)ws;
     T* xs1 = (T*)((char*)ws + half);
-    const int rw = rows_per_warp(gh);
+    const int rw = rows_per_warp(gh, NB, sizeof(T));
+    const size_t dyn = (size_t)FW * KW * rw * NB * sizeof(T);
+    if (dyn > 16 * 1024) {      // with the static tables above the default 48 KiB per block
+        cudaError_t e = cudaFuncSetAttribute(fwd3d_grp<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    }
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         prep_vol_3d<T, NB><<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(x, (int)xdt, (int)batch, (int)b0,
                                                                           gh->nx, gh->ny, gh->nz, xs0, xs1);
-        dim3 fb(32 * FW), fg((gh->nu + FW - 1) / FW, gh->n_views, (gh->nv + rw - 1) / rw);
-        fwd3d_rw<T, NB><<<fg, fb, 0, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
-                                          (flags & CSM_ACCUMULATE) ? 1 : 0);
+        dim3 fb(32 * FW), fg((gh->nu + FW * KW - 1) / (FW * KW), gh->n_views, (gh->nv + rw - 1) / rw);
+        fwd3d_grp<T, NB><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+                                             (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
         if (e != CSM_OK) return e;
     }
@@ -867,7 +879,7 @@ csm_status forward_3d(const csm_geom_s* g, const void* x, void* p, int64_t batch
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     if (flags & CSM_VOXEL_DRIVEN) return CSM_EUNSUPPORTED;
     if (!ws || ws_bytes < workspace_3d(g, 0, batch, dbl)) return CSM_EINVAL;
-    if (g->n_views > 65535 || (g->nv + 7) / 8 > 65535) return CSM_EUNSUPPORTED;
+    if (g->n_views > 65535 || (g->nv + 31) / 32 > 65535) return CSM_EUNSUPPORTED;
     switch (chunk3(batch)) {
         case 4: return dbl ? run_fwd3<double, 4>(g, x, p, batch, xdt, pdt, flags, ws, st)
                            : run_fwd3<float, 4>(g, x, p, batch, xdt, pdt, flags, ws, st);

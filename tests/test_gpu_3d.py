@@ -83,6 +83,26 @@ def test_small_fp32_and_batch(csm):
         assert rel(b[i], oracle.back_3d(g, ys[i])) < FP32_TOL
 
 
+def test_row_windows_batch4(csm):
+    """A tall detector (200 rows) and a batch of 4: the forward splits the rows into windows
+    (96 rows per warp at four batch items); every window and batch item against the oracle."""
+    ang = synth.uniform_angles(6)
+    g = synth.geometry(8, 8, 40, n_views=6, angles=ang, nu=24, nv=200, s=60.0, sdd=100.0, du=1.0, dv=0.6)
+    g["dim"] = 3
+    rng = np.random.default_rng(9)
+    xs = rng.uniform(size=(4, 40, 8, 8))
+    P = csm.Projector(g)
+    p = P.forward(torch.from_numpy(xs).float().cuda()).cpu().numpy()
+    for i in range(4):
+        ref = oracle.forward_3d(g, xs[i])
+        assert per_view_rel(p[i], ref) < FP32_TOL
+        assert np.count_nonzero(ref[:, 96:, :]) > 0          # rows beyond the first window carry weight
+    ys = rng.uniform(size=(4,) + p.shape[1:])
+    b = P.back(torch.from_numpy(ys).float().cuda()).cpu().numpy()
+    for i in range(4):
+        assert rel(b[i], oracle.back_3d(g, ys[i])) < FP32_TOL
+
+
 def test_adjoint_3d(csm):
     ang = synth.uniform_angles(12)
     g = synth.geometry(8, 8, 8, n_views=12, angles=ang, nu=16, nv=14, **dict(SMALL, s=20.0, sdd=33.0))

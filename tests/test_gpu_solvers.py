@@ -46,9 +46,28 @@ def test_power_norm_matches_sparse(mods):
     assert abs(sig - smax) < 1e-3 * smax
 
 
+def _cgls_ref(W, b, iters):
+    """Plain FP64 CGLS on an explicit matrix: iterates and squared residuals per iteration."""
+    x = np.zeros(W.shape[1]); r = b.copy(); s = W.T @ r; d = s.copy(); gam = s @ s
+    xs, hist = [x.copy()], [r @ r]
+    for _ in range(iters):
+        q = W @ d; al = gam / (q @ q); x = x + al * d; r = r - al * q; s = W.T @ r
+        gn = s @ s; d = s + (gn / gam) * d; gam = gn
+        xs.append(x.copy()); hist.append(r @ r)
+    return np.array(xs), np.array(hist)
+
+
 def test_cgls_matches_fp64_reference(mods):
     """50 CGLS iterations on the 64^2 fan-beam problem against a plain FP64 CGLS on the
-    oracle's explicit W."""
+    oracle's explicit W.
+
+    CG on these noisy, ill-posed problems amplifies rounding erratically: perturbing W by a
+    relative 1e-15 moves the reference's own iterate by up to ~1e-3 at some iterations and
+    by ~1e-9 at others, and single residuals by up to a few percent.  So the test measures
+    that spread itself (three references with W perturbed by +-1e-15) and compares the GPU
+    iterate tightly (1e-6) at every iteration where the reference is insensitive (spread
+    below 1e-8); the first nine residuals within 1e-8; the residual never grows; the final
+    residual within 5 %."""
     csm, solvers, _ = mods
     g = synth.config("fan2d_64")
     W = sparse_W(g)
@@ -57,23 +76,34 @@ def test_cgls_matches_fp64_reference(mods):
     p_noisy = np.stack([synth.poisson_sinogram(pi, seed=i)[0] for i, pi in enumerate(p)])
     P = csm.Projector(g)
     cg = solvers.CGLS(P, 2, dtype=torch.float64)
-    x, res2 = cg.run(torch.from_numpy(p_noisy).cuda(), iters=50)
-    x, res2 = x.cpu().numpy(), res2.cpu().numpy()
+    iters = 50
+    res2 = torch.zeros(iters + 1, 2, dtype=torch.float64, device="cuda")
+    cg.start(torch.from_numpy(p_noisy).cuda())
+    cg.ops.dot(cg.r, cg.r, res2[0])
+    xs_gpu = [cg.x.cpu().numpy().reshape(2, -1)]
+    for k in range(iters):
+        cg.step(res2[k + 1])
+        xs_gpu.append(cg.x.cpu().numpy().reshape(2, -1))
+    xs_gpu, res2 = np.stack(xs_gpu), res2.cpu().numpy()
+    rng = np.random.default_rng(0)
+    coo = W.tocoo()
     for i in range(2):
         b = p_noisy[i].ravel()
-        xr = np.zeros(W.shape[1]); r = b.copy(); s = W.T @ r; d = s.copy(); gam = s @ s
-        hist = [r @ r]
-        for _ in range(50):
-            q = W @ d; al = gam / (q @ q); xr += al * d; r -= al * q; s = W.T @ r
-            gn = s @ s; d = s + (gn / gam) * d; gam = gn; hist.append(r @ r)
-        hist = np.array(hist)
-        # CG amplifies rounding: on this noisy problem a 1e-15 relative perturbation of W
-        # alone moves single residuals by a few percent after ~15 iterations and the
-        # 50-iteration iterate by ~4e-5.  Compare the early iterations tightly, the iterate
-        # to 1e-3, and check that the residual never grows.
+        xr, hist = _cgls_ref(W, b, iters)
+        spread = np.zeros(iters + 1)
+        for _ in range(3):
+            Wp = sp.csr_matrix((coo.data * (1 + 1e-15 * rng.choice([-1.0, 1.0], size=coo.nnz)), (coo.row, coo.col)),
+                               shape=W.shape)
+            xp, _ = _cgls_ref(Wp, b, iters)
+            spread = np.maximum(spread, np.linalg.norm(xp - xr, axis=1) / np.maximum(np.linalg.norm(xr, axis=1), 1e-300))
+        quiet = [k for k in range(1, iters + 1) if spread[k] < 1e-8]
+        assert len(quiet) >= 10, quiet
+        for k in quiet:
+            d = np.linalg.norm(xs_gpu[k, i] - xr[k]) / np.linalg.norm(xr[k])
+            assert d < 1e-6, (i, k, d)
         assert np.max(np.abs(res2[:9, i] - hist[:9]) / hist[:9]) < 1e-8
-        assert np.linalg.norm(x[i].ravel() - xr) < 1e-3 * np.linalg.norm(xr)
         assert np.all(np.diff(res2[:, i]) <= 1e-9 * res2[:-1, i])
+        assert abs(res2[iters, i] - hist[iters]) <= 0.05 * hist[iters]
 
 
 def test_cgls_fp32_fan512_sinograms(mods):
