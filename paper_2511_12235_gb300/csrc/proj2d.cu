@@ -158,63 +158,77 @@ __device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict
 }
 
 // ---------------------------------------------------------------------------------------
-// Forward, ray-driven: one thread per (view, element).  The thread walks the cells of its
-// fan strip along the view's walk axis; in each walked column it visits the cells between
-// its two corner lines and accumulates  W * x  for NB batch items.  A block holds 16
-// neighbouring elements of 4 neighbouring views: their strips cover nearly the same cells,
-// so a cell fetched into L1 for one view serves the others.
+// Forward, ray-driven: one thread per (view, pair of neighbouring elements k, k+1).  The
+// thread walks the cells of the pair's fan strip (between corner lines k and k+2) along the
+// view's walk axis; in each walked column it visits the cells between the outer lines, loads
+// each cell's NB batch values once and accumulates  W * x  for both elements (their weights
+// are differences of the three lines' cell atoms).  A block holds 16 element pairs of 4
+// neighbouring views: their strips cover nearly the same cells, so a cell fetched into L1
+// for one view serves the others.
 // ---------------------------------------------------------------------------------------
 template <typename T, int NB>
 __global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0, const T* __restrict__ xs1,
                                                  void* __restrict__ p, int pdt, int B, int b_off, T scale,
                                                  int accumulate) {
-    const int k = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int k = (blockIdx.x * 16 + (threadIdx.x & 15)) * 2;
     const int v = blockIdx.y * 4 + (threadIdx.x >> 4);
     if (k >= g.nu || v >= g.n_views) return;
+    const bool two = k + 1 < g.nu;
+    const int kc = two ? k + 2 : k + 1;            // outer line of the pair
     const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
     const int nc = axis == 0 ? g.ny : g.nx;
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
-    const int w0 = g.wrange[2 * ((size_t)v * g.nu + k)], w1 = g.wrange[2 * ((size_t)v * g.nu + k) + 1];
+    const int* wr = g.wrange + 2 * ((size_t)v * g.nu + k);
+    const int w0 = two ? min(wr[0], wr[2]) : wr[0], w1 = two ? max(wr[1], wr[3]) : wr[1];
     using L = typename LineOf<T>::type;
-    L la, lb;
+    L la, lb, lc;
     la.load(g, v, k, w0);
     lb.load(g, v, k + 1, w0);
-    const T ia = inv_of<T>(g, v, k), ib = inv_of<T>(g, v, k + 1);
-    T acc[NB];
+    lc.load(g, v, kc, w0);
+    const T ia = inv_of<T>(g, v, k), ib = inv_of<T>(g, v, k + 1), ic = inv_of<T>(g, v, kc);
+    T acc[NB], acc2[NB];
 #pragma unroll
-    for (int i = 0; i < NB; ++i) acc[i] = T(0);
+    for (int i = 0; i < NB; ++i) acc[i] = acc2[i] = T(0);
     for (int w = w0; w < w1; ++w) {
-        int clo = min(la.cell_lo(), lb.cell_lo());
-        int chi = max(la.cell_hi(), lb.cell_hi());
+        int clo = min(la.cell_lo(), lc.cell_lo());
+        int chi = max(la.cell_hi(), lc.cell_hi());
         const int c0 = max(clo, 0);
         chi = min(chi, nc - 1);
         if (c0 <= chi) {
-            // both lines' cross offsets at the two walk faces, relative to cell c0, converted
+            // the lines' cross offsets at the two walk faces, relative to cell c0, converted
             // once per column; per cell only an integer shift remains
-            T a0, a1, b0, b1;
+            T a0, a1, b0, b1, e0, e1;
             la.offsets(c0, a0, a1);
             lb.offsets(c0, b0, b1);
+            lc.offsets(c0, e0, e1);
             const T* xw = xs + ((size_t)w * Vec<NB>::Q * nc) * Vec<NB>::W;
             for (int c = c0; c <= chi; ++c) {
                 // the cell's values first: their latency overlaps the weight arithmetic
                 Cell<T, NB> cell;
                 cell.load(xw + (size_t)c * Vec<NB>::W, (size_t)nc * Vec<NB>::W);
-                const T fa = cell_atom(a0, a1, ia), fb = cell_atom(b0, b1, ib);
-                const T wt = sigma > 0 ? fb - fa : fa - fb;
+                const T fa = cell_atom(a0, a1, ia), fb = cell_atom(b0, b1, ib), fc = cell_atom(e0, e1, ic);
+                const T wt = sigma > 0 ? fb - fa : fa - fb, wt2 = sigma > 0 ? fc - fb : fb - fc;
                 cell.fma(acc, wt);
+                cell.fma(acc2, wt2);
                 a0 -= T(1);
                 a1 -= T(1);
                 b0 -= T(1);
                 b1 -= T(1);
+                e0 -= T(1);
+                e1 -= T(1);
             }
         }
         la.step();
         lb.step();
+        lc.step();
     }
 #pragma unroll
     for (int i = 0; i < NB; ++i) {
         const int b = b_off + i;
-        if (b < B) store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k, pdt, acc[i] * scale, accumulate != 0);
+        if (b < B) {
+            store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k, pdt, acc[i] * scale, accumulate != 0);
+            if (two) store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k + 1, pdt, acc2[i] * scale, accumulate != 0);
+        }
     }
 }
 
@@ -284,7 +298,7 @@ __device__ __forceinline__ bool pixel_elements(const Geo& g, int v, T X0, T X1, 
 // block (views v = g, g + BG, ...); each thread loops over its views and the elements of its
 // footprint accumulating  W * p  in registers, then the groups' partial sums are added in
 // shared memory in a fixed order (deterministic, no atomics).  The same cell atoms as the
-// forward kernel give bit-identical entries.
+// forward kernel give the same entries up to the FP32 rounding of the offsets.
 // ---------------------------------------------------------------------------------------
 constexpr int BTX = 16, BTY = 4, BG = 4;   // pixel tile 16 x 4, 4 view groups: 256 threads
 
@@ -391,7 +405,7 @@ static csm_status run_forward(const csm_geom_s* gh, const void* x, void* p, int6
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 pb(32, 8), pg((gh->nx + 31) / 32, (gh->ny + 31) / 32);
         prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
-        dim3 fb(64), fg((gh->nu + 15) / 16, (gh->n_views + 3) / 4);
+        dim3 fb(64), fg((gh->nu + 31) / 32, (gh->n_views + 3) / 4);
         fwd2d_ray<T, NB><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
