@@ -493,50 +493,58 @@ __device__ __forceinline__ bool voxel_rows(const Geo& g, T z0w, T z1w, T tmin, T
 }
 
 // Visits every nonzero W(k, l) of voxel iz in the column (ix, iy) for view v through a sink:
-// sink.add(k, l, W) for each entry.  atoms: the column-view's
-// crossing-line atoms; full: the whole-cell atom; scratch: this lane's 2 (kMaxG + 1) slots,
-// 32 elements apart (one per lane of the warp), for Phi per atom on two consecutive row
-// corner planes.
+// sink.add(k, l, W) for each entry.  atoms: the column-view's crossing-line atoms; full: the
+// whole-cell atom.
 template <typename T, typename Sink>
 __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int iy, int iz, const ColumnView<T>& cv,
-                                              const AtomP<T>* atoms, const AtomP<T>& full, T* scratch, Sink& sink) {
+                                              const AtomP<T>* atoms, const AtomP<T>& full, Sink& sink) {
     const T c = G3<T>::c(g);
     const T z0w = G3<T>::z0(g) + iz * c;
     int l0, l1;
     if (!voxel_rows<T>(g, z0w, z0w + c, cv.tmin_w, cv.tmax_w, l0, l1)) return;
     const int ng = cv.ng, na = ng + 1;
-    // PHI(b, j): Phi of atom j (0: the whole cell, j > 0: crossing line j - 1) on the row
-    // corner plane held in buffer b; buffers alternate between the corners r - 1 and r
-#define PHI(b, j) scratch[((b) * (kMaxG + 1) + (j)) * 32]
+    // pc[j] / pp[j]: Phi of atom j (0: the whole cell, j > 0: crossing line j - 1) on the row
+    // corner planes r and r - 1 (registers: the loops over atoms are unrolled, their bounds
+    // are the same in every lane of the warp)
+    T pc[kMaxG + 1], pp[kMaxG + 1];
+#pragma unroll
+    for (int j = 0; j <= kMaxG; ++j) pp[j] = T(0);
 #pragma unroll 1
     for (int r = l0; r <= l1 + 1; ++r) {
-        const int cur = r & 1, prv = cur ^ 1;
         T q, iq;
         const T h = plane_height(g, r, iz, cv.dh, cv.dl, q, iq);   // above the voxel bottom, units of c
         const T m = fabs(q) * cv.margin_c;       // height change across the cell, units of c
         const int cls = h + m <= T(0) ? 0 : (h - m >= T(1) ? 2 : 1);   // below / above / crossing
         const T gw = h * c;
-#pragma unroll 1
-        for (int j = 0; j < na; ++j) {
-            const AtomP<T>& P = j == 0 ? full : atoms[j - 1];
-            PHI(cur, j) = cls == 0 ? T(0) : (cls == 2 ? c * P.A : phi_p<T>(P, gw, q, iq, c));
+#pragma unroll
+        for (int j = 0; j <= kMaxG; ++j) {
+            if (j < na) {
+                const AtomP<T>& P = j == 0 ? full : atoms[j - 1];
+                pc[j] = cls == 0 ? T(0) : (cls == 2 ? c * P.A : phi_p<T>(P, gw, q, iq, c));
+            } else {
+                pc[j] = T(0);
+            }
         }
-        if (r == l0) continue;
-        // W(k, l) = sigma [S(k+1) - S(k)] with S = 0 (empty lines), S_full (whole-cell lines)
-        // or the crossing lines' S, over the element columns k_first .. k_first + ng
-        const int l = r - 1;
-        const T sf = PHI(cur, 0) - PHI(prv, 0);
-        T prevS = cv.sigma > 0 ? T(0) : sf;
-#pragma unroll 1
-        for (int j = 0; j <= ng; ++j) {
-            const T S = j < ng ? PHI(cur, j + 1) - PHI(prv, j + 1) : (cv.sigma > 0 ? sf : T(0));
-            const int k = cv.k_first + j;
-            const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
-            if ((cv.kin || (k >= 0 && k < g.nu)) && wt != T(0)) sink.add(k, l, wt);
-            prevS = S;
+        if (r > l0) {
+            // W(k, l) = sigma [S(k+1) - S(k)] with S = 0 (empty lines), S_full (whole-cell
+            // lines) or the crossing lines' S, over the element columns k_first .. k_first + ng
+            const int l = r - 1;
+            const T sf = pc[0] - pp[0];
+            T prevS = cv.sigma > 0 ? T(0) : sf;
+#pragma unroll
+            for (int j = 0; j <= kMaxG; ++j) {
+                if (j <= ng) {
+                    const T S = j < ng ? pc[j < kMaxG ? j + 1 : kMaxG] - pp[j < kMaxG ? j + 1 : kMaxG] : (cv.sigma > 0 ? sf : T(0));
+                    const int k = cv.k_first + j;
+                    const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
+                    if ((cv.kin || (k >= 0 && k < g.nu)) && wt != T(0)) sink.add(k, l, wt);
+                    prevS = S;
+                }
+            }
         }
+#pragma unroll
+        for (int j = 0; j <= kMaxG; ++j) pp[j] = pc[j];
     }
-#undef PHI
 }
 
 // Sink of the back projection: W p gathered from this view's projections.
@@ -566,7 +574,6 @@ template <typename T, int NB, int ZW>
 __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
                                                       int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
-    __shared__ T scratch_s[BW][2 * (kMaxG + 1) * 32];
     __shared__ T acc_s[BW][NB * ZW];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
@@ -574,7 +581,6 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
     const int ix = col % g.nx, iy = col / g.nx;
     const int zb = blockIdx.y * ZW, ze = min(zb + ZW, g.nz);
     AtomP<T>* atoms = atoms_s[wid];
-    T* scratch = scratch_s[wid] + lane;
     T* acc = acc_s[wid];                                  // acc[b * ZW + (iz - zb)]
     for (int i = lane; i < NB * ZW; i += 32) acc[i] = T(0);
     for (int v = 0; v < g.n_views; ++v) {
@@ -595,7 +601,7 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
         for (int iz = z0 + lane; iz <= z1; iz += 32) {
 #pragma unroll
             for (int i = 0; i < NB; ++i) sink.sum[i] = T(0);
-            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, sink);
+            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
 #pragma unroll
             for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sink.sum[i];
         }
@@ -643,14 +649,13 @@ struct RowSink {
         }
     }
 };
-constexpr int FWD_SMEM = 24 * 1024;  // shared-memory budget of one block's row sums (6 blocks / SM)
+constexpr int FWD_SMEM = 24 * 1024;  // shared-memory budget of one block's row sums
 
 template <typename T, int NB>
 __global__ void __launch_bounds__(32 * FW, 6) fwd3d_grp(Geo g, int rw, const T* __restrict__ xs0,
                                                      const T* __restrict__ xs1, void* __restrict__ p, int pdt,
                                                      int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[FW][kMaxG + 1];
-    __shared__ T scratch_s[FW][2 * (kMaxG + 1) * 32];
     extern __shared__ __align__(16) unsigned char fwd_dyn[];   // [FW][KW][rw][NB] sums
     using L = typename LineOf<T>::type;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -662,7 +667,6 @@ __global__ void __launch_bounds__(32 * FW, 6) fwd3d_grp(Geo g, int rw, const T* 
     T* rows = reinterpret_cast<T*>(fwd_dyn) + (size_t)wid * KW * rw * NB;   // [(k - kg) * rw + row][NB]
     for (int i = lane; i < KW * rw * NB; i += 32) rows[i] = T(0);
     AtomP<T>* atoms = atoms_s[wid];
-    T* scratch = scratch_s[wid] + lane;
     const int axis = g.axis_sigma[2 * v];
     const int nc = axis == 0 ? g.ny : g.nx;
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
@@ -738,7 +742,7 @@ __global__ void __launch_bounds__(32 * FW, 6) fwd3d_grp(Geo g, int rw, const T* 
                 RowSink<T, NB> sink{rows, rw, kg, nk, L0, nrow};
 #pragma unroll
                 for (int i = 0; i < NB; ++i) sink.xv[i] = xv[i];
-                voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, sink);
+                voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
             }
         }
         la.step();
@@ -767,14 +771,12 @@ struct CountSink {
 
 __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long long* counter) {
     __shared__ AtomP<float> atoms_s[BW][kMaxG + 1];
-    __shared__ float scratch_s[BW][2 * (kMaxG + 1) * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;
     const int ix = col % g.nx, iy = col / g.nx;
     const int zb = blockIdx.y * ZWN, ze = min(zb + ZWN, g.nz);
     AtomP<float>* atoms = atoms_s[wid];
-    float* scratch = scratch_s[wid] + lane;
     const float thr = 1e-6f * g.a * g.b * g.c;
     unsigned long long cnt = 0;
     for (int v = 0; v < g.n_views; ++v) {
@@ -791,7 +793,7 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
         __syncwarp();
         CountSink sink{thr, 0ull};
         for (int iz = z0 + lane; iz <= z1; iz += 32)
-            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], scratch, sink);
+            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
         cnt += sink.n;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
