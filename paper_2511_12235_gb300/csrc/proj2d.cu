@@ -158,22 +158,23 @@ __device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict
 }
 
 // ---------------------------------------------------------------------------------------
-// Forward, ray-driven: one thread per (view, pair of neighbouring elements k, k+1).  The
-// thread walks the cells of the pair's fan strip (between corner lines k and k+2) along the
-// view's walk axis; in each walked column it visits the cells between the outer lines, loads
-// each cell's NB batch values once and accumulates  W * x  for both elements (their weights
-// are differences of the three lines' cell atoms).  A block holds 16 element pairs of 4
-// neighbouring views: their strips cover nearly the same cells, so a cell fetched into L1
-// for one view serves the others.
+// Forward, ray-driven: one thread per (view, pair of neighbouring elements k, k+1) (E = 2;
+// one element per thread, E = 1, when pairs would leave too few threads).  The thread walks
+// the cells of its fan strip (between corner lines k and k+E) along the view's walk axis; in
+// each walked column it visits the cells between the outer lines, loads each cell's NB batch
+// values once and accumulates  W * x  for its elements (their weights are differences of
+// neighbouring lines' cell atoms).  A block holds 16 threads of each of 4 neighbouring views:
+// their strips cover nearly the same cells, so a cell fetched into L1 for one view serves
+// the others.
 // ---------------------------------------------------------------------------------------
-template <typename T, int NB>
+template <typename T, int NB, int E>
 __global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0, const T* __restrict__ xs1,
                                                  void* __restrict__ p, int pdt, int B, int b_off, T scale,
                                                  int accumulate) {
-    const int k = (blockIdx.x * 16 + (threadIdx.x & 15)) * 2;
+    const int k = (blockIdx.x * 16 + (threadIdx.x & 15)) * E;
     const int v = blockIdx.y * 4 + (threadIdx.x >> 4);
     if (k >= g.nu || v >= g.n_views) return;
-    const bool two = k + 1 < g.nu;
+    const bool two = E == 2 && k + 1 < g.nu;
     const int kc = two ? k + 2 : k + 1;            // outer line of the pair
     const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
     const int nc = axis == 0 ? g.ny : g.nx;
@@ -206,10 +207,14 @@ __global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0
                 // the cell's values first: their latency overlaps the weight arithmetic
                 Cell<T, NB> cell;
                 cell.load(xw + (size_t)c * Vec<NB>::W, (size_t)nc * Vec<NB>::W);
-                const T fa = cell_atom(a0, a1, ia), fb = cell_atom(b0, b1, ib), fc = cell_atom(e0, e1, ic);
-                const T wt = sigma > 0 ? fb - fa : fa - fb, wt2 = sigma > 0 ? fc - fb : fb - fc;
+                const T fa = cell_atom(a0, a1, ia), fb = cell_atom(b0, b1, ib);
+                const T wt = sigma > 0 ? fb - fa : fa - fb;
                 cell.fma(acc, wt);
-                cell.fma(acc2, wt2);
+                if constexpr (E == 2) {
+                    const T fc = cell_atom(e0, e1, ic);
+                    const T wt2 = sigma > 0 ? fc - fb : fb - fc;
+                    cell.fma(acc2, wt2);
+                }
                 a0 -= T(1);
                 a1 -= T(1);
                 b0 -= T(1);
@@ -405,9 +410,15 @@ static csm_status run_forward(const csm_geom_s* gh, const void* x, void* p, int6
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 pb(32, 8), pg((gh->nx + 31) / 32, (gh->ny + 31) / 32);
         prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
-        dim3 fb(64), fg((gh->nu + 31) / 32, (gh->n_views + 3) / 4);
-        fwd2d_ray<T, NB><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
-                                           (flags & CSM_ACCUMULATE) ? 1 : 0);
+        // pairs of elements per thread when that still leaves 64 Ki threads
+        const bool pair = (size_t)(gh->nu / 2) * gh->n_views >= 65536;
+        dim3 fb(64), fg(pair ? (gh->nu + 31) / 32 : (gh->nu + 15) / 16, (gh->n_views + 3) / 4);
+        if (pair)
+            fwd2d_ray<T, NB, 2><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+                                                  (flags & CSM_ACCUMULATE) ? 1 : 0);
+        else
+            fwd2d_ray<T, NB, 1><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+                                                  (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
         if (e != CSM_OK) return e;
     }

@@ -620,7 +620,8 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
 
 // ---------------------------------------------------------------------------------------
 // Forward projection, ray-driven over element groups: one warp per (view, group of KW
-// neighbouring detector columns kg .. kg+KW-1, window of rw consecutive rows).  The warp
+// neighbouring detector columns kg .. kg+KW-1, window of rw consecutive rows; KW = 8 when
+// that still gives 16384 warps, else 4).  The warp
 // walks the union of the group's top-view strips cell by cell (as in 2D); per cell it
 // classifies the group's KW + 1 corner lines (column_view restricted to them), builds the
 // tables of the crossing ones (one (line, piece) per lane; the whole-cell table is built once
@@ -633,7 +634,6 @@ __global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict
 // rows for one FP32 batch item).
 // ---------------------------------------------------------------------------------------
 constexpr int FW = 4;                // warps per block
-constexpr int KW = 4;                // detector columns per warp
 
 // Sink of the forward projection: W x added to the (column, row) sums of the warp's group.
 template <typename T, int NB>
@@ -651,8 +651,8 @@ struct RowSink {
 };
 constexpr int FWD_SMEM = 24 * 1024;  // shared-memory budget of one block's row sums
 
-template <typename T, int NB>
-__global__ void __launch_bounds__(32 * FW, 6) fwd3d_grp(Geo g, int rw, const T* __restrict__ xs0,
+template <typename T, int NB, int KW>
+__global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo g, int rw, const T* __restrict__ xs0,
                                                      const T* __restrict__ xs1, void* __restrict__ p, int pdt,
                                                      int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[FW][kMaxG + 1];
@@ -805,9 +805,24 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
 // ---------------------------------------------------------------------------------------
 // Rows per forward warp: all of them when the block's row sums fit the shared-memory budget,
 // else the largest window that does (at least 32 rows).
-static int rows_per_warp(const csm_geom_s* g, int nb, size_t elem) {
-    const int cap = (int)(FWD_SMEM / ((size_t)FW * KW * nb * elem));
+static int rows_per_warp(const csm_geom_s* g, int kw, int nb, size_t elem) {
+    const int cap = (int)(FWD_SMEM / ((size_t)FW * kw * nb * elem));
     return std::max(32, std::min(g->nv, cap));
+}
+
+template <typename T, int NB, int KW>
+static csm_status launch_fwd3(const Geo& g, const csm_geom_s* gh, const T* xs0, const T* xs1, void* p,
+                              int64_t batch, csm_dtype pdt, int64_t b0, T scale, int flags, cudaStream_t st) {
+    const int rw = rows_per_warp(gh, KW, NB, sizeof(T));
+    const size_t dyn = (size_t)FW * KW * rw * NB * sizeof(T);
+    if (dyn > 16 * 1024) {      // with the static tables above the default 48 KiB per block
+        cudaError_t e = cudaFuncSetAttribute(fwd3d_grp<T, NB, KW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    }
+    dim3 fb(32 * FW), fg((gh->nu + FW * KW - 1) / (FW * KW), gh->n_views, (gh->nv + rw - 1) / rw);
+    fwd3d_grp<T, NB, KW><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+                                              (flags & CSM_ACCUMULATE) ? 1 : 0);
+    return check_launch();
 }
 
 template <typename T, int NB>
@@ -820,19 +835,12 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
     T* xs0 = (T*)ws;
     T* xs1 = (T*)((char*)ws + half);
-    const int rw = rows_per_warp(gh, NB, sizeof(T));
-    const size_t dyn = (size_t)FW * KW * rw * NB * sizeof(T);
-    if (dyn > 16 * 1024) {      // with the static tables above the default 48 KiB per block
-        cudaError_t e = cudaFuncSetAttribute(fwd3d_grp<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
-    }
+    const bool wide = (size_t)((gh->nu + 7) / 8) * gh->n_views >= 16384;
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         prep_vol_3d<T, NB><<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(x, (int)xdt, (int)batch, (int)b0,
                                                                           gh->nx, gh->ny, gh->nz, xs0, xs1);
-        dim3 fb(32 * FW), fg((gh->nu + FW * KW - 1) / (FW * KW), gh->n_views, (gh->nv + rw - 1) / rw);
-        fwd3d_grp<T, NB><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
-                                             (flags & CSM_ACCUMULATE) ? 1 : 0);
-        csm_status e = check_launch();
+        csm_status e = wide ? launch_fwd3<T, NB, 8>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st)
+                            : launch_fwd3<T, NB, 4>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st);
         if (e != CSM_OK) return e;
     }
     return CSM_OK;
