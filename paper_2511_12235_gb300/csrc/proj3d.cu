@@ -571,7 +571,7 @@ constexpr int BW = 4;     // warps (columns) per block
 constexpr int ZWN = 64;   // voxels of a column per warp in the nnz count
 
 template <typename T, int NB, int ZW>
-__global__ void __launch_bounds__(32 * BW) back3d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
+__global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
                                                       int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
     __shared__ T acc_s[BW][NB * ZW];
