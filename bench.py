@@ -447,7 +447,7 @@ def run_serving(args, rank, world, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serving", "requests": n, "share_2d": float((kinds == 2).mean()),
                    "nag_iterations": 20, "power_iterations": 20, "budget_gb": 120, "max_active": 16,
-                   "priority_levels": len(srv.levels),
+                   "priority_levels": len(srv.levels), "class_caps": list(srv.caps.values()), "aging": srv.aging,
                    "arrival_rate_per_s": rate, "load_vs_capacity": args.load},
         "throughput": {"served_requests_per_s": n / makespan, "unbatched_requests_per_s": n / float(np.sum(service)),
                        "served_makespan_s": makespan, "unbatched_makespan_s": float(np.sum(service)),

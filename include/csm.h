@@ -56,8 +56,8 @@ typedef enum { CSM_F32 = 0, CSM_F64 = 1, CSM_BF16 = 2, CSM_F16 = 3 } csm_dtype;
 #define CSM_ACCUMULATE        1   /* add into the output instead of overwriting it           */
 #define CSM_RELATIVE_WEIGHTS  2   /* entries divided by the voxel measure ab (abc), as in the
                                      paper's A_3, A_4, Vol_rel                                */
-#define CSM_VOXEL_DRIVEN      4   /* forward only: voxel-driven scatter variant (else the
-                                     ray-driven gather variant)                               */
+#define CSM_VOXEL_DRIVEN      4   /* forward only: the voxel-driven scatter variant; not built
+                                     (CSM_EUNSUPPORTED): the ray-driven gather is the forward */
 
 /* 2D fan-beam geometry.  angles == NULL means phi_v = 2 pi v / n_views. */
 typedef struct {
@@ -92,7 +92,10 @@ typedef struct {
  * Errors: CSM_EINVAL (NULL / non-positive sizes), CSM_EGEOM, CSM_ENOMEM, CSM_ECUDA. */
 csm_status csm_geom_create_2d(const csm_geom2d_desc* desc, csm_geom_t* out);
 
-/* Same for the 3D geometry (Section "The Three-dimensional Case"). */
+/* Same for the 3D geometry (Section "The Three-dimensional Case").  Also CSM_EUNSUPPORTED
+ * when the largest footprint of one voxel in a view exceeds the kernels' per-voxel slots
+ * (its height over dv, plus 3, above 8 row corners; its width over du, rounded down, plus 1
+ * above 6 crossing corner lines), or when nv * nu >= 2^31. */
 csm_status csm_geom_create_3d(const csm_geom3d_desc* desc, csm_geom_t* out);
 
 /* Release the geometry (synchronises the device with cudaFree).  NULL is ignored. */
@@ -109,15 +112,19 @@ csm_status csm_workspace_bytes(csm_geom_t geom, int op, int64_t batch, csm_dtype
  *   p : device pointer, p_dt elements, layout p[batch][n_views][nv][nu]
  *   Arithmetic is FP64 when x_dt or p_dt is CSM_F64, else FP32 (BF16/F16 are storage
  *   types only).  workspace: device pointer of at least csm_workspace_bytes(op = 0);
- *   may alias neither x nor p.  Returns CSM_EINVAL when the workspace is too small. */
+ *   may alias neither x nor p.  Returns CSM_EINVAL when the workspace is too small.
+ *   Ray-driven gather: each element of p is written once.  2D sums in a fixed order
+ *   (bit-reproducible); the 3D forward adds a row's entries through shared-memory atomics
+ *   of one warp, so its FP32 sums may differ in the last bits between runs. */
 csm_status csm_forward(csm_geom_t geom, const void* x, void* p, int64_t batch,
                        csm_dtype x_dt, csm_dtype p_dt, int flags,
                        void* workspace, size_t workspace_bytes, void* cuda_stream);
 
 /* x = W^T p, the adjoint of csm_forward with the same entries (Section "Algorithm 1" and
- * the paper's adjoint-mismatch check, Section "Numerical Experiments").  Gather form: one
- * thread per voxel, no atomics.  Arguments as for csm_forward with the roles of x and p
- * exchanged (workspace from csm_workspace_bytes(op = 1)). */
+ * the paper's adjoint-mismatch check, Section "Numerical Experiments").  Gather form (one
+ * thread per pixel in 2D, one lane per voxel in 3D), fixed summation order, no atomics.
+ * Arguments as for csm_forward with the roles of x and p exchanged (workspace from
+ * csm_workspace_bytes(op = 1)). */
 csm_status csm_back(csm_geom_t geom, const void* p, void* x, int64_t batch,
                     csm_dtype p_dt, csm_dtype x_dt, int flags,
                     void* workspace, size_t workspace_bytes, void* cuda_stream);

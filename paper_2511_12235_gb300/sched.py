@@ -27,3 +27,11 @@ def admit_order(pending, now, slots, running, caps, used, budget, level_of, need
         slots -= 1
         i += 1
     return out
+
+
+def aged_level(class_index: int, waited_s: float, est_service_s):
+    """Priority index (0 = highest) of a request's stream: its cost class, one level higher
+    once it has waited longer than its estimated service time (None: no estimate yet)."""
+    if est_service_s is not None and waited_s > est_service_s and class_index > 0:
+        return class_index - 1
+    return class_index

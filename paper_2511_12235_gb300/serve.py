@@ -15,7 +15,10 @@ Eq. (exp_tikh)).  The server
   before the remaining blocks of long ones: a small request does not wait for a large one to
   drain, which is what a FIFO of whole requests would make it do.  The costlier a class, the
   fewer of its requests run at once (16, 4, 2, 1 for the four classes by default): one large
-  3D solve already fills the GPU, and large requests sharing it would all finish late;
+  3D solve already fills the GPU, and large requests sharing it would all finish late.  A
+  request that has already waited longer than its own estimated service time (its cost
+  times the smallest time per cost seen on completed requests) gets a stream one level
+  higher, so that the requests that waited longest are not also the slowest to run;
 * estimates ||W|| by power iteration on the device (the scalar never leaves the GPU), then
   captures the request's NAG iterations once into a CUDA graph and replays it: the whole
   solve is a single launch;
@@ -36,7 +39,7 @@ import numpy as np
 import torch
 
 from .projector import Projector
-from .sched import admit_order
+from .sched import admit_order, aged_level
 from .solvers import NAG, power_norm2_device
 
 
@@ -97,10 +100,12 @@ class ReconServer:
     the GPU at once; priorities: order streams by request cost (else all at one priority);
     cost_edges: cost thresholds between priority levels (default: decades of
     ``cost_estimate`` from 1e10, the cheapest level highest); level_caps: requests of each
-    level (highest first) that may run at once."""
+    level (highest first) that may run at once; aging: promote requests that waited longer
+    than their estimated service time by one priority level."""
 
     def __init__(self, device="cuda:0", budget_bytes: int = 120 << 30, max_active: int = 16,
-                 use_graphs: bool = True, priorities: bool = True, cost_edges=None, level_caps=None):
+                 use_graphs: bool = True, priorities: bool = True, cost_edges=None, level_caps=None,
+                 aging: bool = True):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.max_active = int(max_active)
@@ -120,6 +125,8 @@ class ReconServer:
                 level_caps[-1] = 1
         self.caps = {lv: max(1, min(int(c), self.max_active)) for lv, c in zip(self.levels, level_caps)}
         self.running = {lv: 0 for lv in self.levels}
+        self.aging = aging
+        self.sec_per_cost = None     # smallest (completion - admission) / cost seen so far
         self.slots = self.max_active
         self._deferred = []          # projectors released once the device is idle
 
@@ -128,12 +135,22 @@ class ReconServer:
         i = sum(1 for e in self.cost_edges if c >= e)
         return self.levels[min(i, len(self.levels) - 1)]
 
+    def stream_level(self, req: Request, now: float) -> int:
+        """Priority of the request's stream: its class level, one level higher when it has
+        waited longer than its estimated service time."""
+        lv = self.level_of(req)
+        if not self.aging or self.sec_per_cost is None:
+            return lv
+        est = self.sec_per_cost * cost_estimate(req.geom, req.iters, req.power_iters)
+        return self.levels[aged_level(self.levels.index(lv), now - req.arrival, est)]
+
     # -----------------------------------------------------------------------------------
     def _launch(self, req: Request, now: float) -> _Active:
         self.slots -= 1
         lv = self.level_of(req)
         self.running[lv] += 1
-        s = self.pool[lv].pop()
+        plv = self.stream_level(req, now)
+        s = self.pool[plv].pop()
         g = req.geom
         with torch.cuda.device(self.device), torch.cuda.stream(s):
             P = Projector(g, device=self.device)
@@ -162,16 +179,18 @@ class ReconServer:
             done = torch.cuda.Event()
             done.record(s)
         req.t_admit = now
-        act = _Active(req, (lv, s), P, nag, graph, out_host, done, footprint_bytes(g))
+        act = _Active(req, (lv, plv, s), P, nag, graph, out_host, done, footprint_bytes(g))
         return act
 
     def _finish(self, act: _Active, now: float):
         act.req.result = act.out_host.numpy().copy()
         act.req.t_done = now
         self.slots += 1
-        lv, s = act.stream
-        self.pool[lv].append(s)
+        lv, plv, s = act.stream
+        self.pool[plv].append(s)
         self.running[lv] -= 1
+        spc = (now - act.req.t_admit) / cost_estimate(act.req.geom, act.req.iters, act.req.power_iters)
+        self.sec_per_cost = spc if self.sec_per_cost is None else min(self.sec_per_cost, spc)
         self._deferred.append(act.P)
         act.graph = None
         act.nag = None

@@ -3,7 +3,7 @@ import dataclasses
 
 import pytest
 
-from paper_2511_12235_gb300.sched import admit_order  # noqa: E402
+from paper_2511_12235_gb300.sched import admit_order, aged_level  # noqa: E402
 
 
 @dataclasses.dataclass
@@ -39,3 +39,10 @@ def test_memory_blocks_later_requests():
     assert _admit(p) == [0]
     with pytest.raises(ValueError):
         _admit([R(0, 0.0, 0, 101)])
+
+
+def test_aging_promotes_by_one_level():
+    assert aged_level(3, 10.0, None) == 3            # no estimate yet
+    assert aged_level(3, 10.0, 20.0) == 3            # waited less than its service time
+    assert aged_level(3, 30.0, 20.0) == 2            # waited longer: one level higher
+    assert aged_level(0, 30.0, 20.0) == 0            # already at the top
