@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS) + ["serving"])
     ap.add_argument("--requests", type=int, default=60, help="serving: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate / measured capacity")
+    ap.add_argument("--sweep", type=str, default="",
+                    help="serving: further loads to run after --load, comma separated (e.g. 0.5,0.9)")
     ap.add_argument("--dtype", default=None, choices=["f32", "f64", "bf16", "f16"],
                     help="storage dtype of volume and sinogram (default per workload)")
     return ap.parse_args()
@@ -427,21 +429,32 @@ def run_serving(args, rank, world, local):
     results_sat = [r.result for r in reqs]
     # latency: Poisson arrivals at `load` times the unbatched capacity
     cap = 1.0 / float(np.mean(service))
-    rate = args.load * cap
-    rng = np.random.default_rng(1)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
-    for r, a in zip(reqs, arrivals):
-        r.arrival = float(a)
-        r.result = None
-    base_lat = fifo_latencies(arrivals, service)
-    srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
-    done = srv.serve(reqs, realtime=True)
-    lat = [r.latency for r in done]
-    st, bst = latency_stats(lat), latency_stats(base_lat)
+    kinds = np.array([r.geom["dim"] for r in reqs])
+
+    def latency_run(load, seed):
+        rate = load * cap
+        rng = np.random.default_rng(seed)
+        arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+        for r, a in zip(reqs, arrivals):
+            r.arrival = float(a)
+            r.result = None
+        base_lat = np.array(fifo_latencies(arrivals, service))
+        srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
+        done = srv.serve(reqs, realtime=True)
+        lat = np.array([r.latency for r in done])
+        st, bst = latency_stats(lat), latency_stats(base_lat)
+        med = lambda a, k: float(np.median(a[kinds == k])) if (kinds == k).any() else None
+        return srv, rate, {
+            "load_vs_capacity": load, "arrival_rate_per_s": rate,
+            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+            "p50_2d_s": med(lat, 2), "p50_3d_s": med(lat, 3),
+            "unbatched": {"p50_s": bst["p50_s"], "p99_s": bst["p99_s"], "mean_s": bst["mean_s"],
+                          "p50_2d_s": med(base_lat, 2), "p50_3d_s": med(base_lat, 3)}}
+
+    srv, rate, main_run = latency_run(args.load, 1)
     same = all(np.array_equal(a, r.result) or np.allclose(a, r.result, rtol=1e-4, atol=1e-6)
                for a, r in zip(results_sat, reqs))
-    kinds = np.array([r.geom["dim"] for r in reqs])
-    lat_a, blat_a = np.array(lat), np.array(base_lat)
+    sweep = [latency_run(float(ld), 2 + i)[2] for i, ld in enumerate(x for x in args.sweep.split(",") if x)]
     line = {
         "metric": METRIC, "value": n / makespan, "unit": "requests/s", "n_gpus": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -452,15 +465,12 @@ def run_serving(args, rank, world, local):
         "throughput": {"served_requests_per_s": n / makespan, "unbatched_requests_per_s": n / float(np.sum(service)),
                        "served_makespan_s": makespan, "unbatched_makespan_s": float(np.sum(service)),
                        "note": "all requests waiting at t = 0"},
-        "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
-        "p50_2d_s": float(np.median(lat_a[kinds == 2])) if (kinds == 2).any() else None,
-        "p50_3d_s": float(np.median(lat_a[kinds == 3])) if (kinds == 3).any() else None,
-        "unbatched": {"p50_s": bst["p50_s"], "p99_s": bst["p99_s"], "mean_s": bst["mean_s"],
-                      "p50_2d_s": float(np.median(blat_a[kinds == 2])) if (kinds == 2).any() else None,
-                      "p50_3d_s": float(np.median(blat_a[kinds == 3])) if (kinds == 3).any() else None,
-                      "mean_service_s": float(np.mean(service)),
-                      "note": "same requests and arrivals, one at a time with plain csm_forward/csm_back calls "
-                              "(FIFO queue over the measured service times)"},
+        "p50_s": main_run["p50_s"], "p99_s": main_run["p99_s"], "mean_s": main_run["mean_s"],
+        "p50_2d_s": main_run["p50_2d_s"], "p50_3d_s": main_run["p50_3d_s"],
+        "unbatched": dict(main_run["unbatched"], mean_service_s=float(np.mean(service)),
+                          note="same requests and arrivals, one at a time with plain csm_forward/csm_back calls "
+                               "(FIFO queue over the measured service times)"),
+        "load_sweep": sweep,
         "results_equal_across_runs": bool(same),
         "service_s": [round(float(x), 4) for x in service],
     }

@@ -148,15 +148,6 @@ template <int NB> struct Cell<double, NB> {
     }
 };
 
-// acc[b] += wt * value[b] for the NB items of one cell; `base` points at the cell's first
-// vector and consecutive planes are `plane` elements apart.
-template <typename T, int NB>
-__device__ __forceinline__ void fma_cell(T (&acc)[NB], T wt, const T* __restrict__ base, size_t plane) {
-    Cell<T, NB> cell;
-    cell.load(base, plane);
-    cell.fma(acc, wt);
-}
-
 // ---------------------------------------------------------------------------------------
 // Forward, ray-driven: one thread per (view, pair of neighbouring elements k, k+1) (E = 2;
 // one element per thread, E = 1, when pairs would leave too few threads).  The thread walks

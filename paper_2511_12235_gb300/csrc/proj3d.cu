@@ -48,8 +48,6 @@ size_t workspace_3d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
     return sino;
 }
 
-template <int NB> struct Vec3 { static constexpr int W = NB; };
-
 template <typename T>
 __device__ __forceinline__ T load_any3(const void* base, size_t i, int dt) {
     switch (dt) {

@@ -55,6 +55,22 @@ def test_fan64_fp64_forward_back_full(csm):
     assert np.max(np.abs(b - b_ref)) < 1e-11 * np.max(np.abs(b_ref))
 
 
+def test_element_pairs_odd_detector_fp64(csm):
+    """Enough views and elements that the forward runs one thread per element pair, with an
+    odd element count (the last pair has one element): FP64 against the oracle."""
+    ang = synth.uniform_angles(512)
+    g = synth.geometry(24, 20, 1, n_views=512, angles=ang, s=60.0, sdd=100.0, nu=257, du=0.18, u_off=0.1)
+    assert (g["nu"] // 2) * g["n_views"] >= 65536
+    rng = np.random.default_rng(3)
+    x = rng.uniform(size=(2, 20, 24))
+    P = csm.Projector(g)
+    p = P.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    for i in range(2):
+        ref = oracle.forward_2d(g, x[i])
+        assert per_view_rel(p[i], ref) < FP64_TOL
+        assert np.count_nonzero(ref[:, -1]) > 0          # the unpaired last element carries weight
+
+
 def test_fan64_fp32(csm):
     g = synth.config("fan2d_64")
     x = synth.ellipse_phantom(64, 0)
