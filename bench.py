@@ -328,6 +328,8 @@ def run_ours(args, rank, world, local):
 
     updates_per_step = 2.0 * nnz * batch * world
     value = updates_per_step * args.steps / (t_ms / 1e3) / 1e9
+    # (voxel, view) pairs visited by the two projections, per second
+    voxel_views = 2.0 * g["nx"] * g["ny"] * g["nz"] * g["n_views"] * batch * world * args.steps / (t_ms / 1e3) / 1e9
     e2e_value = updates_per_step * args.steps / (t_e2e / 1e3) / 1e9
 
     # roofline of the dominant kernel (ALU bound: algorithmic flops / launch time)
@@ -348,6 +350,7 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed before every timed step (512 MiB write, untimed)",
                    "step": "forward over all views + back projection of the batch"},
         "gpu_launches": 4 * args.steps,
+        "gvoxel_views_per_s": voxel_views,
         "kernels_ms": {"forward": t_fwd, "back": t_back},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": dram_traffic(wl, dom),
@@ -367,10 +370,16 @@ def run_ours(args, rank, world, local):
             pq = oracle.forward_2d(gq, xq, views=views)
             oracle.back_2d(gq, pq, views=views)
             dt = time.perf_counter() - t0
+            # parity of the timed forward (batch item 0, the same phantom) on the sampled views
+            p_gpu = P.forward(x)[0].double().cpu().numpy()[views]
+            num = np.linalg.norm(p_gpu - pq, axis=1)
+            den = np.linalg.norm(pq, axis=1)
+            rel = float(np.max(num[den > 0] / den[den > 0]))
             line["cpu_baseline"] = {
                 "value": 2.0 * n_sample / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": "FP64 oracle fwd+back of 1 phantom over %d of 720 views (%d entries), %.1f s"
-                          % (len(views), n_sample, dt)}
+                          % (len(views), n_sample, dt),
+                "forward_parity_max_rel_l2_per_view": rel}
         except Exception as e:  # the baseline is reported, not required
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                     "sample": "failed: %s" % e}

@@ -19,9 +19,11 @@ Eq. (exp_tikh)).  The server
   request that has already waited longer than its own estimated service time (its cost
   times the smallest time per cost seen on completed requests) gets a stream one level
   higher, so that the requests that waited longest are not also the slowest to run;
-* estimates ||W|| by power iteration on the device (the scalar never leaves the GPU), then
-  captures the request's NAG iterations once into a CUDA graph and replays it: the whole
-  solve is a single launch;
+* estimates ||W|| by power iteration on the device (the scalar never leaves the GPU) once
+  per geometry: the start vector is seeded by the geometry, so the estimate is a function of
+  the geometry alone and later requests of the same geometry reuse it (after an event on the
+  stream that computed it); then captures the request's NAG iterations once into a CUDA
+  graph and replays it: the whole solve is a single launch;
 * polls completion events and returns results with their latency.
 
 All device work is in the library's kernels; the server only orders it.  Results do not
@@ -39,7 +41,7 @@ import numpy as np
 import torch
 
 from .projector import Projector
-from .sched import admit_order, aged_level
+from .sched import admit_order, aged_level, geometry_key, geometry_seed
 from .solvers import NAG, power_norm2_device
 
 
@@ -52,7 +54,7 @@ class Request:
     iters: int = 20
     lam: float = 1e-4
     power_iters: int = 20
-    seed: int = 0
+    seed: int = 0                    # caller's tag (the power iteration is seeded by the geometry)
     result: np.ndarray | None = None
     t_admit: float | None = None
     t_done: float | None = None
@@ -127,6 +129,8 @@ class ReconServer:
         self.running = {lv: 0 for lv in self.levels}
         self.aging = aging
         self.sec_per_cost = None     # smallest (completion - admission) / cost seen so far
+        self.sigma_cache = {}        # (geometry key, power iterations) -> (||W||^2 on the device, event)
+        self.sigma_hits = 0
         self.slots = self.max_active
         self._deferred = []          # projectors released once the device is idle
 
@@ -156,10 +160,22 @@ class ReconServer:
             P = Projector(g, device=self.device)
             data = torch.from_numpy(np.ascontiguousarray(req.sino, dtype=np.float32)).pin_memory()
             p = data.to(self.device, non_blocking=True).reshape((1,) + tuple(P.sino_shape))
-            gen = torch.Generator(device=self.device)
-            gen.manual_seed(req.seed)
-            start = torch.randn((1,) + tuple(P.vol_shape), generator=gen, device=self.device, dtype=torch.float32)
-            sig2 = power_norm2_device(P, iters=req.power_iters, start=start)
+            key = (geometry_key(g), req.power_iters)
+            hit = self.sigma_cache.get(key)
+            if hit is None:
+                gen = torch.Generator(device=self.device)
+                gen.manual_seed(geometry_seed(g))
+                start = torch.randn((1,) + tuple(P.vol_shape), generator=gen, device=self.device,
+                                    dtype=torch.float32)
+                sig2 = power_norm2_device(P, iters=req.power_iters, start=start)
+                ev = torch.cuda.Event()
+                ev.record(s)
+                self.sigma_cache[key] = (sig2, ev)
+            else:
+                sig2, ev = hit
+                s.wait_event(ev)
+                sig2.record_stream(s)         # read on this stream too
+                self.sigma_hits += 1
             # an estimated norm: a 1% margin keeps the step 1 / (1 + lam) below 1 / L
             nag = NAG(P, 1, lam=req.lam, sigma2_device=sig2, sigma_scale=1.01)
             nag.start(p)
@@ -249,7 +265,7 @@ def solve_alone(req: Request, device="cuda:0") -> np.ndarray:
     P = Projector(req.geom, device=dev)
     p = torch.from_numpy(np.ascontiguousarray(req.sino, dtype=np.float32)).to(dev).reshape((1,) + tuple(P.sino_shape))
     gen = torch.Generator(device=dev)
-    gen.manual_seed(req.seed)
+    gen.manual_seed(geometry_seed(req.geom))
     start = torch.randn((1,) + tuple(P.vol_shape), generator=gen, device=dev, dtype=torch.float32)
     sig2 = power_norm2_device(P, iters=req.power_iters, start=start)
     nag = NAG(P, 1, lam=req.lam, sigma2_device=sig2, sigma_scale=1.01)

@@ -72,3 +72,24 @@ def test_priority_follows_cost():
     assert srv.level_of(rs) <= srv.level_of(rb)
     if len(srv.levels) > 1:
         assert srv.level_of(rs) < srv.level_of(rb)
+
+
+def test_norm_cached_per_geometry():
+    """Two requests of one geometry: the second reuses the first's spectral-norm estimate
+    (seeded by the geometry), and both results equal the same requests solved alone."""
+    from paper_2511_12235_gb300 import Projector
+    from paper_2511_12235_gb300.serve import ReconServer, Request, solve_alone
+    g = synth.geometry(64, 64, 1, n_views=80, s=125.0, sdd=187.0, nu=96)
+    P = Projector(g)
+    reqs = []
+    for i in range(2):
+        x = synth.ellipse_phantom(64, 200 + i)
+        sino = P.forward(torch.from_numpy(x).float().cuda()).cpu().numpy()
+        reqs.append(Request(id=i, geom=g, sino=sino, arrival=0.0, iters=6, power_iters=8))
+    P.close()
+    alone = [solve_alone(r) for r in reqs]
+    srv = ReconServer(max_active=2, use_graphs=True)
+    done = srv.serve(reqs, realtime=False)
+    assert srv.sigma_hits == 1
+    for r, a in zip(sorted(done, key=lambda r: r.id), alone):
+        assert np.array_equal(r.result, a), r.id

@@ -46,3 +46,16 @@ def test_aging_promotes_by_one_level():
     assert aged_level(3, 10.0, 20.0) == 3            # waited less than its service time
     assert aged_level(3, 30.0, 20.0) == 2            # waited longer: one level higher
     assert aged_level(0, 30.0, 20.0) == 0            # already at the top
+
+
+def test_geometry_key():
+    from paper_2511_12235_gb300.sched import geometry_key, geometry_seed
+    import numpy as np
+    import synth
+    g1 = synth.geometry(64, 64, 1, n_views=90, s=200.0, sdd=400.0, nu=96)
+    g2 = synth.geometry(64, 64, 1, n_views=90, s=200.0, sdd=400.0, nu=96)
+    g3 = synth.geometry(64, 64, 1, n_views=90, s=200.0, sdd=400.0, nu=96, angles=synth.uniform_angles(90) + 1e-9)
+    g4 = synth.geometry(64, 64, 1, n_views=90, s=200.0, sdd=401.0, nu=96)
+    assert geometry_key(g1) == geometry_key(g2) and geometry_seed(g1) == geometry_seed(g2)
+    assert len({geometry_key(g) for g in (g1, g3, g4)}) == 3
+    assert 0 <= geometry_seed(g1) < 2 ** 63
