@@ -24,7 +24,10 @@ Eq. (exp_tikh)).  The server
   the geometry alone and later requests of the same geometry reuse it (after an event on the
   stream that computed it); then captures the request's NAG iterations once into a CUDA
   graph and replays it: the whole solve is a single launch;
-* polls completion events and returns results with their latency.
+* polls completion events and returns results with their latency.  A request that cannot
+  run (its geometry is refused, its projections have the wrong size, it needs more memory
+  than the whole budget, or its set-up fails with an out-of-memory error) is returned with
+  `error` set and no result; the others are served as usual.
 
 All device work is in the library's kernels; the server only orders it.  Results do not
 depend on which other requests run at the same time beyond rounding: every kernel sees only
@@ -40,6 +43,7 @@ import time
 import numpy as np
 import torch
 
+from ._capi import CsmError
 from .projector import Projector
 from .sched import admit_order, aged_level, geometry_key, geometry_seed
 from .solvers import NAG, power_norm2_device
@@ -58,6 +62,7 @@ class Request:
     result: np.ndarray | None = None
     t_admit: float | None = None
     t_done: float | None = None
+    error: str | None = None         # why the request could not run (then result is None)
 
     @property
     def latency(self) -> float:
@@ -150,11 +155,20 @@ class ReconServer:
 
     # -----------------------------------------------------------------------------------
     def _launch(self, req: Request, now: float) -> _Active:
-        self.slots -= 1
         lv = self.level_of(req)
-        self.running[lv] += 1
         plv = self.stream_level(req, now)
         s = self.pool[plv].pop()
+        self.slots -= 1
+        self.running[lv] += 1
+        try:
+            return self._start(req, now, lv, plv, s)
+        except Exception:
+            self.slots += 1
+            self.running[lv] -= 1
+            self.pool[plv].append(s)
+            raise
+
+    def _start(self, req: Request, now: float, lv: int, plv: int, s) -> _Active:
         g = req.geom
         with torch.cuda.device(self.device), torch.cuda.stream(s):
             P = Projector(g, device=self.device)
@@ -226,6 +240,11 @@ class ReconServer:
         if not realtime:
             for r in pending:
                 r.arrival = 0.0
+        for r in [r for r in pending if footprint_bytes(r.geom) > self.budget]:
+            r.error = "needs %d bytes of device memory, more than the budget of %d" % (footprint_bytes(r.geom),
+                                                                                       self.budget)
+            r.t_done = r.arrival
+            pending.remove(r)
         active = []
         used = 0
         t0 = time.perf_counter()
@@ -236,8 +255,12 @@ class ReconServer:
                               self.level_of, lambda r: footprint_bytes(r.geom))
             for i in idx:
                 req = pending[i]
-                active.append(self._launch(req, time.perf_counter() - t0))
-                used += footprint_bytes(req.geom)
+                try:
+                    active.append(self._launch(req, time.perf_counter() - t0))
+                    used += footprint_bytes(req.geom)
+                except (CsmError, ValueError, RuntimeError) as e:   # this request cannot run
+                    req.error = "%s: %s" % (type(e).__name__, e)
+                    req.t_done = time.perf_counter() - t0
             for i in reversed(idx):
                 pending.pop(i)
             # completions

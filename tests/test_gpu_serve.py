@@ -93,3 +93,28 @@ def test_norm_cached_per_geometry():
     assert srv.sigma_hits == 1
     for r, a in zip(sorted(done, key=lambda r: r.id), alone):
         assert np.array_equal(r.result, a), r.id
+
+
+def test_failing_requests_do_not_stop_the_others():
+    """A refused geometry, projections of the wrong size and a request larger than the whole
+    budget come back with `error` set; the valid request is served as alone."""
+    from paper_2511_12235_gb300 import Projector
+    from paper_2511_12235_gb300.serve import ReconServer, Request, footprint_bytes, solve_alone
+    good = synth.geometry(48, 48, 1, n_views=60, s=94.0, sdd=141.0, nu=72)
+    P = Projector(good)
+    sino = P.forward(torch.from_numpy(synth.ellipse_phantom(48, 5)).float().cuda()).cpu().numpy()
+    P.close()
+    inside = synth.geometry(48, 48, 1, n_views=60, s=20.0, sdd=141.0, nu=72)   # source inside the grid
+    big = synth.geometry(48, 48, 1, n_views=60, s=94.0, sdd=141.0, nu=72)
+    reqs = [Request(id=0, geom=good, sino=sino, iters=5, power_iters=6),
+            Request(id=1, geom=inside, sino=sino, iters=5, power_iters=6),
+            Request(id=2, geom=good, sino=sino[:, :-1].copy(), iters=5, power_iters=6),
+            Request(id=3, geom=big, sino=sino, iters=5, power_iters=6)]
+    srv = ReconServer(budget_bytes=2 * footprint_bytes(good), max_active=4, use_graphs=True)
+    # request 3 claims a footprint above the budget
+    reqs[3].geom = dict(big, nz=10 ** 6)
+    done = {r.id: r for r in srv.serve(reqs, realtime=False)}
+    assert done[0].error is None and np.array_equal(done[0].result, solve_alone(reqs[0]))
+    for i in (1, 2, 3):
+        assert done[i].error and done[i].result is None, (i, done[i].error)
+    assert srv.slots == srv.max_active and all(v == 0 for v in srv.running.values())
