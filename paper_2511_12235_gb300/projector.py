@@ -1,17 +1,28 @@
 """PyTorch front end of the C ABI: geometry handles, forward / back on CUDA tensors.
 
 PyTorch supplies device memory and the current stream only; every step of the projection
-runs in the library's CUDA kernels (``_capi``).
+runs in the library's CUDA kernels (``_capi``).  With the environment variable CSM_NVTX=1 the
+calls are wrapped in NVTX ranges ("csm_forward", "csm_back") for timeline profilers.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes as C
 import math
+import os
 
 import numpy as np
 import torch
 
 from . import _capi as capi
+
+_NVTX = os.environ.get("CSM_NVTX", "") == "1"
+
+
+def nvtx_range(name: str):
+    """An NVTX range around a block when CSM_NVTX=1, else nothing."""
+    return torch.cuda.nvtx.range(name) if _NVTX else contextlib.nullcontext()
+
 
 _DT = {torch.float32: capi.CSM_F32, torch.float64: capi.CSM_F64,
        torch.bfloat16: capi.CSM_BF16, torch.float16: capi.CSM_F16}
@@ -111,8 +122,9 @@ class Projector:
         compute = torch.float64 if torch.float64 in (xb.dtype, out.dtype) else torch.float32
         ws = self.workspace(0, B, compute)
         stream = torch.cuda.current_stream(self.device).cuda_stream
-        capi.csm_forward(self.handle, xb.data_ptr(), out.data_ptr(), B, _dt(xb.dtype), _dt(out.dtype), flags,
-                         ws.data_ptr(), ws.numel(), stream)
+        with nvtx_range("csm_forward"):
+            capi.csm_forward(self.handle, xb.data_ptr(), out.data_ptr(), B, _dt(xb.dtype), _dt(out.dtype), flags,
+                             ws.data_ptr(), ws.numel(), stream)
         return out[0] if single else out
 
     def back(self, p: torch.Tensor, out: torch.Tensor | None = None, *, flags: int = 0,
@@ -132,8 +144,9 @@ class Projector:
         compute = torch.float64 if torch.float64 in (pb.dtype, out.dtype) else torch.float32
         ws = self.workspace(1, B, compute)
         stream = torch.cuda.current_stream(self.device).cuda_stream
-        capi.csm_back(self.handle, pb.data_ptr(), out.data_ptr(), B, _dt(pb.dtype), _dt(out.dtype), flags,
-                      ws.data_ptr(), ws.numel(), stream)
+        with nvtx_range("csm_back"):
+            capi.csm_back(self.handle, pb.data_ptr(), out.data_ptr(), B, _dt(pb.dtype), _dt(out.dtype), flags,
+                          ws.data_ptr(), ws.numel(), stream)
         return out[0] if single else out
 
     def nnz(self) -> int:

@@ -16,7 +16,7 @@ import math
 import torch
 
 from . import _capi as capi
-from .projector import Projector, _dt
+from .projector import Projector, _dt, nvtx_range
 
 
 class VecOps:
@@ -118,6 +118,10 @@ class CGLS:
         self.cur = 0
 
     def step(self, res2_out: torch.Tensor | None = None):
+        with nvtx_range("cgls_step"):
+            self._step(res2_out)
+
+    def _step(self, res2_out):
         P, ops = self.P, self.ops
         g_old, g_new = self.gam[self.cur], self.gam[1 - self.cur]
         P.forward(self.d, out=self.q)
@@ -195,6 +199,10 @@ class NAG:
         return out
 
     def step(self):
+        with nvtx_range("nag_step"):
+            self._step()
+
+    def _step(self):
         ops = self.ops
         step = 1.0 / (1.0 + self.lam)
         self.gradient(self.y, self.g)
