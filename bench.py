@@ -435,6 +435,7 @@ def run_serving(args, rank, world, local):
     t0 = time.perf_counter()
     srv.serve(reqs, realtime=False)
     makespan = time.perf_counter() - t0
+    srv.close()
     results_sat = [r.result for r in reqs]
     # latency: Poisson arrivals at `load` times the unbatched capacity
     cap = 1.0 / float(np.mean(service))
@@ -450,6 +451,7 @@ def run_serving(args, rank, world, local):
         base_lat = np.array(fifo_latencies(arrivals, service))
         srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
         done = srv.serve(reqs, realtime=True)
+        srv.close()
         lat = np.array([r.latency for r in done])
         st, bst = latency_stats(lat), latency_stats(base_lat)
         med = lambda a, k: float(np.median(a[kinds == k])) if (kinds == k).any() else None

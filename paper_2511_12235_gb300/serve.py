@@ -23,7 +23,11 @@ Eq. (exp_tikh)).  The server
   per geometry: the start vector is seeded by the geometry, so the estimate is a function of
   the geometry alone and later requests of the same geometry reuse it (after an event on the
   stream that computed it); then captures the request's NAG iterations once into a CUDA
-  graph and replays it: the whole solve is a single launch;
+  graph and replays it: the whole solve is a single launch.  A finished solve (projector,
+  solver state, graph) is kept per shape bucket -- geometry, iterations, lambda -- and a
+  later request of the same bucket loads its projections into it, resets the iterate and
+  replays the graph, with no new allocation or capture; idle solves count against the memory
+  budget and are released, oldest first, when an admission needs the memory;
 * polls completion events and returns results with their latency.  A request that cannot
   run (its geometry is refused, its projections have the wrong size, it needs more memory
   than the whole budget, or its set-up fails with an out-of-memory error) is returned with
@@ -96,9 +100,18 @@ def footprint_bytes(geom: dict, elem: int = 4) -> int:
     return elem * (7 * nvox + 4 * nsino) + table + (1 << 20)
 
 
+class _Solve:
+    """A request's device state: projector, NAG state, the captured graph of its iterations,
+    the buffers the graph starts from and the one it leaves the iterate in."""
+
+    def __init__(self, key, P, nag, graph, u0, y0, u_out, nbytes):
+        self.key, self.P, self.nag, self.graph = key, P, nag, graph
+        self.u0, self.y0, self.u_out, self.nbytes = u0, y0, u_out, nbytes
+
+
 class _Active:
-    def __init__(self, req, stream, P, nag, graph, out_host, done, nbytes):
-        self.req, self.stream, self.P, self.nag, self.graph = req, stream, P, nag, graph
+    def __init__(self, req, stream, solve, out_host, done, nbytes):
+        self.req, self.stream, self.solve = req, stream, solve
         self.out_host, self.done, self.nbytes = out_host, done, nbytes
 
 
@@ -108,11 +121,12 @@ class ReconServer:
     cost_edges: cost thresholds between priority levels (default: decades of
     ``cost_estimate`` from 1e10, the cheapest level highest); level_caps: requests of each
     level (highest first) that may run at once; aging: promote requests that waited longer
-    than their estimated service time by one priority level."""
+    than their estimated service time by one priority level; max_idle: finished solves kept
+    for reuse by later requests of their shape bucket."""
 
     def __init__(self, device="cuda:0", budget_bytes: int = 120 << 30, max_active: int = 16,
                  use_graphs: bool = True, priorities: bool = True, cost_edges=None, level_caps=None,
-                 aging: bool = True):
+                 aging: bool = True, max_idle: int = 4):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.max_active = int(max_active)
@@ -136,6 +150,9 @@ class ReconServer:
         self.sec_per_cost = None     # smallest (completion - admission) / cost seen so far
         self.sigma_cache = {}        # (geometry key, power iterations) -> (||W||^2 on the device, event)
         self.sigma_hits = 0
+        self.max_idle = int(max_idle) if use_graphs else 0
+        self.idle = []               # finished solves kept for reuse, oldest first
+        self.graph_hits = 0
         self.slots = self.max_active
         self._deferred = []          # projectors released once the device is idle
 
@@ -170,47 +187,67 @@ class ReconServer:
 
     def _start(self, req: Request, now: float, lv: int, plv: int, s) -> _Active:
         g = req.geom
+        bucket = (geometry_key(g), req.iters, req.power_iters, float(req.lam))
+        sv = None
+        for i, cand in enumerate(self.idle):
+            if cand.key == bucket:
+                sv = self.idle.pop(i)
+                break
         with torch.cuda.device(self.device), torch.cuda.stream(s):
-            P = Projector(g, device=self.device)
             data = torch.from_numpy(np.ascontiguousarray(req.sino, dtype=np.float32)).pin_memory()
-            p = data.to(self.device, non_blocking=True).reshape((1,) + tuple(P.sino_shape))
-            key = (geometry_key(g), req.power_iters)
-            hit = self.sigma_cache.get(key)
-            if hit is None:
-                gen = torch.Generator(device=self.device)
-                gen.manual_seed(geometry_seed(g))
-                start = torch.randn((1,) + tuple(P.vol_shape), generator=gen, device=self.device,
-                                    dtype=torch.float32)
-                sig2 = power_norm2_device(P, iters=req.power_iters, start=start)
-                ev = torch.cuda.Event()
-                ev.record(s)
-                self.sigma_cache[key] = (sig2, ev)
+            if sv is not None:
+                # same shape bucket: load the data, reset the iterate, replay the graph
+                if data.numel() != sv.nag.p.numel():
+                    raise ValueError("projections of %d values for a geometry of %d" % (data.numel(), sv.nag.p.numel()))
+                sv.nag.p.copy_(data.reshape(sv.nag.p.shape), non_blocking=True)
+                sv.u0.zero_()
+                sv.y0.zero_()
+                sv.graph.replay()
+                self.graph_hits += 1
             else:
-                sig2, ev = hit
-                s.wait_event(ev)
-                sig2.record_stream(s)         # read on this stream too
-                self.sigma_hits += 1
-            # an estimated norm: a 1% margin keeps the step 1 / (1 + lam) below 1 / L
-            nag = NAG(P, 1, lam=req.lam, sigma2_device=sig2, sigma_scale=1.01)
-            nag.start(p)
-            graph = None
-            if self.use_graphs:
-                graph = torch.cuda.CUDAGraph()
-                graph.capture_begin()
-                for _ in range(req.iters):
-                    nag.step()
-                graph.capture_end()
-                graph.replay()
-            else:
-                for _ in range(req.iters):
-                    nag.step()
-            out_host = torch.empty(tuple(P.vol_shape), dtype=torch.float32).pin_memory()
-            out_host.copy_(nag.u[0], non_blocking=True)
+                sv = self._new_solve(req, bucket, data, s)
+            out_host = torch.empty(tuple(sv.P.vol_shape), dtype=torch.float32).pin_memory()
+            out_host.copy_(sv.u_out[0], non_blocking=True)
             done = torch.cuda.Event()
             done.record(s)
         req.t_admit = now
-        act = _Active(req, (lv, plv, s), P, nag, graph, out_host, done, footprint_bytes(g))
-        return act
+        return _Active(req, (lv, plv, s), sv, out_host, done, footprint_bytes(g))
+
+    def _new_solve(self, req: Request, bucket, data, s) -> _Solve:
+        g = req.geom
+        P = Projector(g, device=self.device)
+        p = data.to(self.device, non_blocking=True).reshape((1,) + tuple(P.sino_shape))
+        key = (geometry_key(g), req.power_iters)
+        hit = self.sigma_cache.get(key)
+        if hit is None:
+            gen = torch.Generator(device=self.device)
+            gen.manual_seed(geometry_seed(g))
+            start = torch.randn((1,) + tuple(P.vol_shape), generator=gen, device=self.device, dtype=torch.float32)
+            sig2 = power_norm2_device(P, iters=req.power_iters, start=start)
+            ev = torch.cuda.Event()
+            ev.record(s)
+            self.sigma_cache[key] = (sig2, ev)
+        else:
+            sig2, ev = hit
+            s.wait_event(ev)
+            sig2.record_stream(s)         # read on this stream too
+            self.sigma_hits += 1
+        # an estimated norm: a 1% margin keeps the step 1 / (1 + lam) below 1 / L
+        nag = NAG(P, 1, lam=req.lam, sigma2_device=sig2, sigma_scale=1.01)
+        nag.start(p)
+        u0, y0 = nag.u, nag.y
+        graph = None
+        if self.use_graphs:
+            graph = torch.cuda.CUDAGraph()
+            graph.capture_begin()
+            for _ in range(req.iters):
+                nag.step()
+            graph.capture_end()
+            graph.replay()
+        else:
+            for _ in range(req.iters):
+                nag.step()
+        return _Solve(bucket, P, nag, graph, u0, y0, nag.u, footprint_bytes(g))
 
     def _finish(self, act: _Active, now: float):
         act.req.result = act.out_host.numpy().copy()
@@ -221,9 +258,22 @@ class ReconServer:
         self.running[lv] -= 1
         spc = (now - act.req.t_admit) / cost_estimate(act.req.geom, act.req.iters, act.req.power_iters)
         self.sec_per_cost = spc if self.sec_per_cost is None else min(self.sec_per_cost, spc)
-        self._deferred.append(act.P)
-        act.graph = None
-        act.nag = None
+        sv = act.solve
+        act.solve = None
+        if self.max_idle > 0 and sv.graph is not None:
+            self.idle.append(sv)
+            while len(self.idle) > self.max_idle:
+                self._drop(self.idle.pop(0))
+        else:
+            self._drop(sv)
+
+    def _drop(self, sv: _Solve):
+        self._deferred.append(sv.P)
+        sv.graph = None
+        sv.nag = None
+
+    def idle_bytes(self) -> int:
+        return sum(sv.nbytes for sv in self.idle)
 
     def _release_deferred(self):
         # freeing a geometry table synchronises the device; done only when it is idle
@@ -250,9 +300,14 @@ class ReconServer:
         t0 = time.perf_counter()
         while pending or active:
             now = time.perf_counter() - t0
-            # admit in arrival order while memory and a slot of the request's class are free
-            idx = admit_order(pending, now, self.slots, self.running, self.caps, used, self.budget,
-                              self.level_of, lambda r: footprint_bytes(r.geom))
+            # admit in arrival order while memory and a slot of the request's class are free; idle
+            # solves hold memory too and are released, oldest first, when a request needs it
+            idx = admit_order(pending, now, self.slots, self.running, self.caps, used + self.idle_bytes(),
+                              self.budget, self.level_of, lambda r: footprint_bytes(r.geom))
+            while not idx and self.idle and pending and pending[0].arrival <= now and self.slots > 0:
+                self._drop(self.idle.pop(0))
+                idx = admit_order(pending, now, self.slots, self.running, self.caps, used + self.idle_bytes(),
+                                  self.budget, self.level_of, lambda r: footprint_bytes(r.geom))
             for i in idx:
                 req = pending[i]
                 try:
@@ -279,6 +334,13 @@ class ReconServer:
         torch.cuda.synchronize(self.device)
         self._release_deferred()
         return requests
+
+    def close(self):
+        """Release the idle solves and their geometry tables."""
+        while self.idle:
+            self._drop(self.idle.pop(0))
+        torch.cuda.synchronize(self.device)
+        self._release_deferred()
 
 
 def solve_alone(req: Request, device="cuda:0") -> np.ndarray:

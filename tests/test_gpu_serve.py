@@ -118,3 +118,27 @@ def test_failing_requests_do_not_stop_the_others():
     for i in (1, 2, 3):
         assert done[i].error and done[i].result is None, (i, done[i].error)
     assert srv.slots == srv.max_active and all(v == 0 for v in srv.running.values())
+
+
+def test_graph_reused_per_shape_bucket():
+    """A second request of the same geometry (after the first finished) replays the first's
+    captured graph in its solve state; results equal the requests solved alone."""
+    from paper_2511_12235_gb300 import Projector
+    from paper_2511_12235_gb300.serve import ReconServer, Request, solve_alone
+    ga = synth.geometry(48, 48, 1, n_views=64, s=94.0, sdd=141.0, nu=72)
+    gb = synth.geometry(40, 40, 1, n_views=50, s=79.0, sdd=118.0, nu=60)
+    reqs = []
+    for i, g in enumerate((ga, gb, ga)):
+        P = Projector(g)
+        x = synth.ellipse_phantom(g["nx"], 300 + i)
+        reqs.append(Request(id=i, geom=g, sino=P.forward(torch.from_numpy(x).float().cuda()).cpu().numpy(),
+                            arrival=0.0, iters=7, power_iters=8))
+        P.close()
+    alone = [solve_alone(r) for r in reqs]
+    srv = ReconServer(max_active=1, use_graphs=True)      # one at a time: request 2 finds request 0 idle
+    done = srv.serve(reqs, realtime=False)
+    assert srv.graph_hits == 1
+    for r, a in zip(sorted(done, key=lambda r: r.id), alone):
+        assert np.array_equal(r.result, a), r.id
+    srv.close()
+    assert not srv.idle
