@@ -275,6 +275,18 @@ class ReconServer:
     def idle_bytes(self) -> int:
         return sum(sv.nbytes for sv in self.idle)
 
+    def _memory_blocked(self, pending, now, used) -> bool:
+        """Whether the next request admission would take (the first arrived one whose class
+        has a free slot) waits for memory."""
+        for r in pending:
+            if r.arrival > now:
+                return False
+            lv = self.level_of(r)
+            if self.running[lv] >= self.caps[lv]:
+                continue
+            return used + self.idle_bytes() + footprint_bytes(r.geom) > self.budget
+        return False
+
     def _release_deferred(self):
         # freeing a geometry table synchronises the device; done only when it is idle
         for P in self._deferred:
@@ -304,7 +316,7 @@ class ReconServer:
             # solves hold memory too and are released, oldest first, when a request needs it
             idx = admit_order(pending, now, self.slots, self.running, self.caps, used + self.idle_bytes(),
                               self.budget, self.level_of, lambda r: footprint_bytes(r.geom))
-            while not idx and self.idle and pending and pending[0].arrival <= now and self.slots > 0:
+            while not idx and self.idle and self.slots > 0 and self._memory_blocked(pending, now, used):
                 self._drop(self.idle.pop(0))
                 idx = admit_order(pending, now, self.slots, self.running, self.caps, used + self.idle_bytes(),
                                   self.budget, self.level_of, lambda r: footprint_bytes(r.geom))
