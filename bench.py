@@ -143,17 +143,22 @@ def measured_peaks():
 
 
 def kernel_source_hash() -> str:
-    """sha256 over the CUDA sources and the C header (names and bytes, sorted by name)."""
+    """sha256 over the CUDA sources and the C header (sorted by name) with comments and
+    whitespace removed, so that only a change of the code itself changes it."""
     import glob
     import hashlib
+    import re
     csrc = os.path.join(ROOT, "paper_2511_12235_gb300", "csrc")
     files = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh")))
     files.append(os.path.join(ROOT, "include", "csm.h"))
     h = hashlib.sha256()
     for f in files:
+        with open(f) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)       # block comments
+        text = re.sub(r"//[^\n]*", " ", text)                    # line comments
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()
 
 

@@ -1,5 +1,6 @@
-// proj3d.cu -- 3D circular cone-beam projectors: p = W x (ray-driven gather over row
-// bundles) and x = W^T p (voxel-driven gather), every entry W_ij evaluated on the fly.
+// proj3d.cu -- 3D circular cone-beam projectors: p = W x (ray-driven gather, a warp per
+// group of detector columns) and x = W^T p (voxel-driven gather, a warp per voxel column),
+// every entry W_ij evaluated on the fly.
 //
 // Entry (Section "The Three-dimensional Case"): the volume of voxel j inside the pyramid of
 // element (k, l), i.e. between the lateral planes of corners k, k+1 (the 2D rays, seen from
@@ -18,13 +19,10 @@
 // (the paper restricts its experiments to three).
 //
 // Each Phi is two integrals of relu(g + q t') over the polygon R (t' = depth relative to the
-// cell centre).  They are evaluated exactly: 0 when the linear function is <= 0 on R,
-// g A + q M1 when it is >= 0 on R, and otherwise by the divergence theorem as a sum over
-// R's edges,  -(1/q) sum_e w_e E3(l_P, l_Q),  where w_e is the outward edge normal (times
-// length) projected on the source direction and E3 the exact mean of relu^2 / 2 along the
-// edge.  These are the paper's cubic terms C g^3 (Eq. (rel vol 3d), Eq. (res vol 3d)) written
-// per edge instead of per vertex, which removes the 1/sin(phi), 1/cos(phi) factors of the
-// printed forms (their singular views, Eq. (vol)) from the arithmetic.
+// cell centre), i.e. the tail moment M(T) = integral over R of relu(t' - T) dA at the two
+// kinks.  M is a cubic in T between consecutive vertex depths of R; each atom gets a table of
+// those pieces (see "Tail-moment table" below), from the divergence-theorem edge sum that is
+// the paper's cubic terms C g^3 (Eq. (rel vol 3d), Eq. (res vol 3d)) written per edge.
 #include <algorithm>
 
 #include "csm_internal.cuh"
