@@ -194,3 +194,23 @@ def test_batch_invariance(csm):
     b16 = P.back(y).cpu().numpy()
     for b in (1, 2, 11):
         assert np.array_equal(P.back(y[:b]).cpu().numpy(), b16[:b]), b
+
+
+def test_empty_and_zero_inputs(csm):
+    """A batch of zero items returns empty outputs without launching; zero inputs give exact
+    zeros (2D and 3D, both directions)."""
+    g2 = synth.config("fan2d_64")
+    g3 = synth.geometry(6, 5, 7, n_views=5, s=14.0, sdd=23.0, nu=14, nv=12, a=1.2, b=0.9, c=1.1)
+    g3["dim"] = 3
+    for g in (g2, g3):
+        P = csm.Projector(g)
+        for dt in (torch.float32, torch.float64):
+            x0 = torch.zeros((0,) + P.vol_shape, dtype=dt, device="cuda")
+            p0 = torch.zeros((0,) + P.sino_shape, dtype=dt, device="cuda")
+            assert P.forward(x0).shape == (0,) + P.sino_shape
+            assert P.back(p0).shape == (0,) + P.vol_shape
+            z = torch.zeros((2,) + P.vol_shape, dtype=dt, device="cuda")
+            assert int(torch.count_nonzero(P.forward(z))) == 0
+            zp = torch.zeros((2,) + P.sino_shape, dtype=dt, device="cuda")
+            assert int(torch.count_nonzero(P.back(zp))) == 0
+        torch.cuda.synchronize()
