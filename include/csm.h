@@ -23,6 +23,8 @@
  *   sinogram  p[batch][n_views][nv][nu]   (2D: nv = 1)
  *
  * Every call is asynchronous on the given CUDA stream (NULL = legacy default stream).
+ * A geometry belongs to the device that was current when it was created: csm_forward,
+ * csm_back and csm_nnz return CSM_EINVAL when another device is current.
  * Argument errors are returned synchronously; a failed kernel launch returns
  * CSM_ECUDA.  Nothing aborts the process.  The library owns only the device geometry
  * table created by csm_geom_create_*; every other buffer (inputs, outputs, workspace)
@@ -98,7 +100,8 @@ csm_status csm_geom_create_2d(const csm_geom2d_desc* desc, csm_geom_t* out);
  * above 6 crossing corner lines), or when nv * nu >= 2^31. */
 csm_status csm_geom_create_3d(const csm_geom3d_desc* desc, csm_geom_t* out);
 
-/* Release the geometry (synchronises the device with cudaFree).  NULL is ignored. */
+/* Release the geometry (synchronises its device with cudaFree; the table is released on the
+ * device that holds it and the caller's current device is restored).  NULL is ignored. */
 void csm_geom_free(csm_geom_t geom);
 
 /* Bytes of caller-provided device workspace that csm_forward / csm_back need for this
@@ -167,12 +170,28 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
  * the library until exit), so batch may not exceed CSM_DOT_NOALLOC_MAX_BATCH: larger
  * batches return CSM_EINVAL.  Result and arguments otherwise as csm_dot (same kernels, same
  * summation order).  The first call on a device looks up the array's device address with
- * that device current; make that first call before any stream capture.  All calls share the
+ * that device current (and caches it with the identifier of the device's CUDA context, so a
+ * call after cudaDeviceReset looks it up again); make that first call before any stream
+ * capture.  All calls share the
  * one array: calls that may overlap on the GPU (different streams, or different host
  * threads) race and must be serialised by the caller.  No allocation is made. */
 #define CSM_DOT_NOALLOC_MAX_BATCH 64
 csm_status csm_dot_noalloc(const void* a, const void* c, int64_t n, int64_t batch, csm_dtype dt,
                            double* out, void* cuda_stream);
+
+/* ---- measurement ----------------------------------------------------------------------
+ * The paper has no counterpart: this measures the roofline that bounds the projectors.
+ * Their entries are geometry evaluated with plain FP32 (FP64) arithmetic, so the binding
+ * peak is the device's fused multiply-add issue rate, measured here rather than assumed.
+ *
+ * Runs `launches` back-to-back launches of a kernel of independent FMA chains (dt CSM_F32
+ * or CSM_F64; blocks_per_sm blocks of 256 threads on every SM, `iters` x 128 FMAs per
+ * thread) on the stream, timed with CUDA events on that stream, and waits for it.  Returns
+ * the flops executed (2 per FMA) and the elapsed seconds; their ratio is the peak at the
+ * clocks the GPU ran meanwhile.  Allocates nothing.  Errors: CSM_EINVAL (non-positive
+ * counts, other dtypes), CSM_ECUDA. */
+csm_status csm_fma_rate(csm_dtype dt, int64_t iters, int blocks_per_sm, int launches,
+                        double* flops, double* seconds, void* cuda_stream);
 
 /* Waits for the stream and reports an asynchronous kernel failure as CSM_ECUDA. */
 csm_status csm_sync_status(void* cuda_stream);

@@ -9,7 +9,9 @@ code with the CUDA path.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (Monte Carlo, the paper's closed-form atoms, partition and
-column-sum invariants, closed-form fan/pyramid volumes, scaling and symmetry).
+column-sum invariants, closed-form fan/pyramid volumes, scaling and symmetry); the COO
+export, the entry counts and the z-slab back projection are pinned against the projections
+they must reproduce (``tests/test_oracle_coo.py``).
 """
 from __future__ import annotations
 
@@ -84,6 +86,8 @@ def _load():
         lib.orc2d_coo.restype = C.c_long
         lib.orc3d_coo.argtypes = [gp, ip, C.c_int, ip, ip, dp, C.c_long]
         lib.orc3d_coo.restype = C.c_long
+        lib.orc3d_back_slab.argtypes = [gp, dp, dp, ip, C.c_int, C.c_int, C.c_int]
+        lib.orc3d_back_slab.restype = C.c_long
         lib.orc2d_count.argtypes = [gp, ip, C.c_int]
         lib.orc2d_count.restype = C.c_long
         lib.orc_num_threads.restype = C.c_int
@@ -212,6 +216,18 @@ def back_3d(g: dict, p: np.ndarray, views=None) -> np.ndarray:
     x = np.zeros((g["nz"], g["ny"], g["nx"]), np.float64)
     _load().orc3d_back(h.ref, _dptr(p), _dptr(x), _iptr(v), len(v))
     return x
+
+
+def back_slab_3d(g: dict, p: np.ndarray, iz0: int, iz1: int, views=None):
+    """x[iz0:iz1] of W^T p over the given views (p is [len(views)][nv][nu]), and the number of
+    nonzero entries that went into it.  Returns (x [iz1 - iz0][ny][nx], count)."""
+    h = _GeomHolder(g)
+    v = _views(g, views)
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    assert p.shape == (len(v), g["nv"], g["nu"]) and 0 <= iz0 <= iz1 <= g["nz"]
+    x = np.zeros((iz1 - iz0, g["ny"], g["nx"]), np.float64)
+    n = _load().orc3d_back_slab(h.ref, _dptr(p), _dptr(x), _iptr(v), len(v), int(iz0), int(iz1))
+    return x, int(n)
 
 
 def forward_element_3d(g: dict, x: np.ndarray, view: int, k: int, l: int) -> float:

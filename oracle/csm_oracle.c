@@ -453,6 +453,31 @@ void orc3d_back(const orc_geom* g, const double* p, double* x, const int* views,
         }
 }
 
+/* x = W^T p on the z-slab iz0 <= iz < iz1 only (x is [iz1 - iz0][ny][nx], p is
+ * [nsel][nv][nu]): the same sums as orc3d_back for those voxels.  Returns the number of
+ * nonzero entries applied (for rate accounting). */
+long orc3d_back_slab(const orc_geom* g, const double* p, double* x, const int* views, int nsel,
+                     int iz0, int iz1) {
+    size_t plane = (size_t)g->nu * g->nv;
+    long total = 0;
+    int nzs = iz1 - iz0;
+    #pragma omp parallel for schedule(dynamic, 1) collapse(2) reduction(+:total)
+    for (int dz = 0; dz < nzs; ++dz)
+        for (int iy = 0; iy < g->ny; ++iy) {
+            int kls[CAP3]; double ws[CAP3];
+            for (int ix = 0; ix < g->nx; ++ix) {
+                double acc = 0.0;
+                for (int vi = 0; vi < nsel; ++vi) {
+                    int n = orc3d_entries(g, views[vi], ix, iy, iz0 + dz, 0, kls, ws, CAP3);
+                    for (int e = 0; e < n; ++e) acc += ws[e] * p[(size_t)vi * plane + kls[e]];
+                    total += n;
+                }
+                x[((size_t)dz * g->ny + iy) * g->nx + ix] = acc;
+            }
+        }
+    return total;
+}
+
 /* One back-projected value x_j = sum over the selected views of W^T p (sampled checks). */
 double orc3d_back_voxel(const orc_geom* g, const double* p, const int* views, int nsel,
                         int ix, int iy, int iz) {

@@ -69,6 +69,9 @@ lib.csm_axpby.argtypes = [C.c_int64, C.c_int64, C.c_int, C.c_double, C.c_void_p,
 lib.csm_axpby.restype = _st
 lib.csm_dot_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]
 lib.csm_dot_noalloc.restype = _st
+lib.csm_fma_rate.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                             C.c_void_p]
+lib.csm_fma_rate.restype = _st
 lib.csm_sync_status.argtypes = [C.c_void_p]
 lib.csm_sync_status.restype = _st
 lib.csm_status_string.argtypes = [_st]
@@ -80,6 +83,7 @@ EXPORTED = [
     "csm_geom_create_2d", "csm_geom_create_3d", "csm_geom_free", "csm_workspace_bytes",
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
     "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
+    "csm_fma_rate",
 ]
 CSM_DOT_NOALLOC_MAX_BATCH = 64
 
@@ -156,3 +160,10 @@ def csm_axpby(n, batch, dt, a_c, a_num, a_den, x_ptr, b_c, b_num, b_den, y_ptr, 
 
 def csm_dot_noalloc(a_ptr, c_ptr, n, batch, dt, out_ptr, stream) -> None:
     check(lib.csm_dot_noalloc(a_ptr, c_ptr, n, batch, dt, out_ptr, stream), "csm_dot_noalloc")
+
+
+def csm_fma_rate(dt, iters, blocks_per_sm, launches, stream) -> tuple[float, float]:
+    """(flops, seconds) of the FMA-chain kernel on the current device."""
+    f, t = C.c_double(), C.c_double()
+    check(lib.csm_fma_rate(dt, iters, blocks_per_sm, launches, C.byref(f), C.byref(t), stream), "csm_fma_rate")
+    return f.value, t.value

@@ -287,6 +287,15 @@ static csm_status finish_create(csm_geom_s* g, const double* angles, csm_geom_t*
 
 static bool pos(double v) { return std::isfinite(v) && v > 0; }
 
+// The geometry's tables live on the device it was created on: a call made with another
+// device current would hand the kernels pointers into another GPU's memory.
+static csm_status check_device(const csm_geom_s* g) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    return dev == g->device ? CSM_OK : CSM_EINVAL;
+}
+
 }  // namespace csm
 
 using namespace csm;
@@ -329,7 +338,14 @@ csm_status csm_geom_create_3d(const csm_geom3d_desc* d, csm_geom_t* out) {
 
 void csm_geom_free(csm_geom_t g) {
     if (!g) return;
-    if (g->d_block) cudaFree(g->d_block);
+    if (g->d_block) {
+        // release the table on the device that holds it, then restore the caller's device
+        int prev = -1;
+        const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
+        if (have_prev && prev != g->device) cudaSetDevice(g->device);
+        cudaFree(g->d_block);
+        if (have_prev && prev != g->device) cudaSetDevice(prev);
+    }
     delete g;
 }
 
@@ -348,6 +364,8 @@ csm_status csm_forward(csm_geom_t g, const void* x, void* p, int64_t batch, csm_
     if (batch == 0) return CSM_OK;
     if (!x || !p) return CSM_EINVAL;
     if (flags & ~(CSM_ACCUMULATE | CSM_RELATIVE_WEIGHTS | CSM_VOXEL_DRIVEN)) return CSM_EINVAL;
+    csm_status dv = check_device(g);
+    if (dv != CSM_OK) return dv;
     cudaStream_t st = (cudaStream_t)stream;
     return g->dim == 2 ? forward_2d(g, x, p, batch, xdt, pdt, flags, ws, ws_bytes, st)
                        : forward_3d(g, x, p, batch, xdt, pdt, flags, ws, ws_bytes, st);
@@ -359,6 +377,8 @@ csm_status csm_back(csm_geom_t g, const void* p, void* x, int64_t batch, csm_dty
     if (batch == 0) return CSM_OK;
     if (!x || !p) return CSM_EINVAL;
     if (flags & ~(CSM_ACCUMULATE | CSM_RELATIVE_WEIGHTS)) return CSM_EINVAL;
+    csm_status dv = check_device(g);
+    if (dv != CSM_OK) return dv;
     cudaStream_t st = (cudaStream_t)stream;
     return g->dim == 2 ? back_2d(g, p, x, batch, pdt, xdt, flags, ws, ws_bytes, st)
                        : back_3d(g, p, x, batch, pdt, xdt, flags, ws, ws_bytes, st);
@@ -367,6 +387,8 @@ csm_status csm_back(csm_geom_t g, const void* p, void* x, int64_t batch, csm_dty
 csm_status csm_nnz(csm_geom_t g, int64_t* nnz, void* stream) {
     if (!g || !nnz) return CSM_EINVAL;
     if (g->nnz >= 0) { *nnz = g->nnz; return CSM_OK; }
+    csm_status dv = check_device(g);
+    if (dv != CSM_OK) return dv;
     int64_t n = 0;
     csm_status st = g->dim == 2 ? nnz_2d(g, &n, (cudaStream_t)stream) : nnz_3d(g, &n, (cudaStream_t)stream);
     if (st == CSM_OK) { g->nnz = n; *nnz = n; }

@@ -124,27 +124,66 @@ static __device__ __align__(256) double g_dot_scratch[kDotNoAllocMaxBatch * kDot
 
 constexpr int kMaxDevices = 64;
 static std::mutex g_scratch_mu;
-static double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchSlot {
+    unsigned long long ctx_id;   // CUDA context the address belongs to (0: none yet)
+    double* addr;
+};
+static ScratchSlot g_scratch[kMaxDevices] = {};
 
-// Device address of g_dot_scratch on the current device.  In host code the array's name
-// denotes a host-side stand-in, so the address is looked up once per device (with that device
-// current) and cached.
+// Identifier of the current CUDA context (unique within the process; 0 when no context is
+// current yet), through the driver entry points that the runtime hands out, so the library
+// needs no link to libcuda.  Called with g_scratch_mu held.
+typedef int (*CtxGetCurrentFn)(void**);
+typedef int (*CtxGetIdFn)(void*, unsigned long long*);
+static CtxGetCurrentFn g_ctx_get_current = nullptr;
+static CtxGetIdFn g_ctx_get_id = nullptr;
+static csm_status current_context_id(unsigned long long* id) {
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2);
+        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2) return CSM_ECUDA;
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    void* ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0) return CSM_ECUDA;
+    *id = 0;
+    if (ctx && g_ctx_get_id(ctx, id) != 0) return CSM_ECUDA;
+    return CSM_OK;
+}
+
+// Device address of g_dot_scratch in the current device's context.  In host code the
+// array's name denotes a host-side stand-in, so the address is looked up with the device
+// current: the first time the device is used, and again whenever its context has changed
+// (after cudaDeviceReset the old address would point into released memory); it is cached
+// per device together with the context's identifier.
 static csm_status dot_scratch_address(double** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     if (dev < 0 || dev >= kMaxDevices) return CSM_EUNSUPPORTED;
     std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    unsigned long long ctx = 0;
+    csm_status s = current_context_id(&ctx);
+    if (s != CSM_OK) return s;
+    ScratchSlot& slot = g_scratch[dev];
+    if (!slot.addr || ctx == 0 || slot.ctx_id != ctx) {
         void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_dot_scratch);
+        e = cudaGetSymbolAddress(&p, g_dot_scratch);   // makes the device's context current
         if (e != cudaSuccess || !p) {
             set_cuda_error(e);
             return CSM_ECUDA;
         }
-        g_scratch_addr[dev] = (double*)p;
+        s = current_context_id(&ctx);
+        if (s != CSM_OK) return s;
+        slot.addr = (double*)p;
+        slot.ctx_id = ctx;
     }
-    *out = g_scratch_addr[dev];
+    *out = slot.addr;
     return CSM_OK;
 }
 
