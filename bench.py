@@ -1,13 +1,15 @@
 #!/usr/bin/env python3
-"""Benchmark: fan-beam forward + back projection with the consistent system matrix.
+"""Benchmark: cone-beam forward + back projection with the consistent system matrix.
 
-Workload (one step): 2D fan beam, 512x512 unit pixels, 720 views over 360 deg, 768
-detector elements of width 1, source-isocentre 1000, source-detector 1500; a batch of 16
-seeded random-ellipse phantoms in FP32; one step = p = W x over all views, then
+Default workload (one step): 3D circular cone beam, 512^3 unit voxels, 360 views over
+360 deg, 768 x 768 detector of unit elements, source-isocentre 1000, source-detector 1500;
+one seeded random-ellipsoid phantom in FP32; one step = p = W x over all views, then
 x' = W^T p.  Metric: G voxel-ray updates per second, an update being one nonzero W_ij
-applied to one batch item, counted 2 nnz(W) B per step (forward + back).
+applied to one batch item, counted 2 nnz(W) B per step (forward + back).  ``--workload``
+selects the other workloads (fan2d_512: 512^2, 720 views, 768 elements, batch 16;
+fan2d_64; cone3d_128) and ``serving`` the reconstruction-serving mix.
 
-Runs one rank per GPU (torchrun for N > 1); every rank projects its own 16 phantoms
+Runs one rank per GPU (torchrun for N > 1); every rank projects its own phantoms
 (independent problems: weak scaling, no data-path collective).  ``--impl reference``
 times the FP64 CPU oracle instead (rank 0 only), on a bounded sample of the same workload.
 """
@@ -26,8 +28,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+back projector Gvoxel-ray updates/s vs FP64 oracle; served recon p50/p99"
 UNIT = "Gupdates/s"
-WORKLOAD = "fan2d_512"
-BATCH = 16
+WORKLOAD = "cone3d_512"
 # other workloads (not the default line): batch and storage dtype
 WORKLOADS = {
     "fan2d_512": dict(batch=16, dtype="f32"),
@@ -41,12 +42,14 @@ WORKLOADS = {
 #       double difference (40 flops)
 FLOPS_PER_ENTRY_WEIGHT = {2: 12, 3: 40}
 L2_FLUSH_BYTES = 512 << 20
+# the reference arm (the oracle) is sized so that all its steps take about this long
+REFERENCE_TOTAL_S = 120.0
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -177,21 +180,42 @@ def dram_traffic(workload: str, kernel: str):
     return float(v) if v is not None else None
 
 
-def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def measure_alu_peak(dev, clocks_gpu: int):
+    """FP32 (and FP64) fused multiply-add rate of this GPU from the library's FMA-chain
+    kernel (csm_fma_rate): a burst (one launch of ~10 ms, for a kernel timed alone) and a
+    sustained figure (back-to-back launches for ~3 s, the last 2 s timed, for a kernel timed
+    inside a long step), with the SM clocks sampled meanwhile.  TFLOP/s."""
+    import torch
+    from paper_2511_12235_gb300 import _capi as capi
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    capi.csm_fma_rate(capi.CSM_F32, 1000, 8, 1, stream)                       # warm-up
+    f, t = capi.csm_fma_rate(capi.CSM_F32, 10000, 8, 1, stream)
+    burst = f / t / 1e12
+    iters = max(1000, int(10000 * 0.05 / max(t, 1e-6)))                       # ~50 ms launches
+    capi.csm_fma_rate(capi.CSM_F32, iters, 8, 20, stream)                     # ~1 s to settle
+    clk = ClockSampler(clocks_gpu)
+    clk.start()
+    f, t = capi.csm_fma_rate(capi.CSM_F32, iters, 8, 40, stream)
+    c = clk.stop()
+    sustained = f / t / 1e12
+    f, t = capi.csm_fma_rate(capi.CSM_F64, 500, 8, 1, stream)
+    fp64 = f / t / 1e12
+    return {"fp32_burst_tflops": burst, "fp32_sustained_tflops": sustained, "fp64_burst_tflops": fp64,
+            "sustained_sm_mhz": c.get("sm_mhz"), "sustained_reasons": c.get("reasons"),
+            "how": "csm_fma_rate: 8 blocks x 256 threads per SM, 8 independent FMA chains per thread; "
+                   "burst = one ~10 ms launch, sustained = 40 back-to-back ~50 ms launches after 1 s"}
 
 
 # ---------------------------------------------------------------------------------------
+# CPU baselines: the FP64 oracle as it stands, on the host cores, on a bounded sample.
 def cpu_oracle_leg(steps: int, target_s: float = 15.0):
-    """Time the FP64 oracle (as it stands) on the host cores on a sample of the workload:
-    forward + back of one phantom over a subset of views.  Returns a dict."""
+    """2D sample: forward + back of one phantom over a subset of views, sized so that one
+    step takes about target_s / steps.  Returns (geometry, phantom, views, threads)."""
     import numpy as np
     import oracle
     import synth
-    g = synth.config(WORKLOAD)
+    g = synth.config("fan2d_512")
     x = synth.ellipse_phantom(512, 0)
-    # calibrate the number of views so that one step takes about target_s / steps
     per_step = max(1.0, target_s / max(steps, 1))
     v_try = [0, 180, 360, 540]
     p = oracle.forward_2d(g, x, views=v_try[:1])   # thread-pool start-up, not timed
@@ -204,34 +228,149 @@ def cpu_oracle_leg(steps: int, target_s: float = 15.0):
     return g, x, views, oracle.num_threads()
 
 
+def cpu_slab_sample(g, target_s: float):
+    """3D sample: the oracle's back projection W^T p of one view (view 0) over a z-slab of the
+    volume, p a seeded uniform [1][nv][nu] sinogram; the slab (centred in z) is sized so that
+    one evaluation takes about target_s.  Returns (p, iz0, iz1)."""
+    import numpy as np
+    import oracle
+    p = np.random.default_rng(2).uniform(size=(1, g["nv"], g["nu"]))
+    mid = g["nz"] // 2
+    oracle.back_slab_3d(g, p, mid, mid + 1, views=[0])             # thread-pool start-up
+    t0 = time.perf_counter()
+    oracle.back_slab_3d(g, p, mid - 2, mid + 2, views=[0])
+    t4 = max(time.perf_counter() - t0, 1e-4) / 4
+    h = int(max(2, min(g["nz"], target_s / t4)))
+    iz0 = max(0, mid - h // 2)
+    return p, iz0, min(g["nz"], iz0 + h)
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    import numpy as np
     import oracle
-    g, x, views, cores = cpu_oracle_leg(args.steps)
-    # updates in the sample: the nonzero entries of those views, counted by the oracle
-    nnz_sample = oracle.count_2d(g, views=views)
-    for _ in range(args.warmup):
-        p = oracle.forward_2d(g, x, views=views)
-        oracle.back_2d(g, p, views=views)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        p = oracle.forward_2d(g, x, views=views)
-        oracle.back_2d(g, p, views=views)
-    dt = time.perf_counter() - t0
-    value = 2.0 * nnz_sample * args.steps / dt / 1e9
-    sample = "oracle FP64 fwd+back of 1 phantom over %d of 720 views (%d nonzero entries)" % (len(views), nnz_sample)
+    import synth
+    wl = getattr(args, "workload", WORKLOAD)
+    if wl not in WORKLOADS:
+        wl = WORKLOAD
+    g = synth.config(wl)
+    if g["dim"] == 3:
+        # each step: the oracle's back projection of one view over a z-slab (bounded sample)
+        per_step = max(0.05, REFERENCE_TOTAL_S / max(args.steps + args.warmup, 1))
+        p, iz0, iz1 = cpu_slab_sample(g, per_step)
+        for _ in range(args.warmup):
+            oracle.back_slab_3d(g, p, iz0, iz1, views=[0])
+        n_upd = 0
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, n = oracle.back_slab_3d(g, p, iz0, iz1, views=[0])
+            n_upd += n
+        dt = time.perf_counter() - t0
+        value = n_upd / dt / 1e9
+        sample = ("oracle FP64 back projection W^T p of view 0 over voxel slices %d..%d of %d (%d nonzero "
+                  "entries per step)" % (iz0, iz1 - 1, g["nz"], n_upd // max(args.steps, 1)))
+        cfg = {"workload": wl + " (sampled: one view, z-slab)", "batch": 1, "views": 1, "slab": [iz0, iz1]}
+    else:
+        g, x, views, _ = cpu_oracle_leg(args.steps)
+        nnz_sample = oracle.count_2d(g, views=views)
+        for _ in range(args.warmup):
+            p = oracle.forward_2d(g, x, views=views)
+            oracle.back_2d(g, p, views=views)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            p = oracle.forward_2d(g, x, views=views)
+            oracle.back_2d(g, p, views=views)
+        dt = time.perf_counter() - t0
+        value = 2.0 * nnz_sample * args.steps / dt / 1e9
+        sample = "oracle FP64 fwd+back of 1 phantom over %d of 720 views (%d nonzero entries)" % (len(views),
+                                                                                               nnz_sample)
+        cfg = {"workload": "fan2d_512 (sampled views)", "batch": 1, "views": int(len(views))}
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD + " (sampled views)", "batch": 1,
-                                        "views": int(len(views))},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def elementwise_rel(got, want):
+    """Largest |got - want| / (|want| + 0.1 max|want|) over the samples: the relative error
+    of every sample, floored at a tenth of the largest value, so that a bound b on it reads
+    |got - want| <= b |want| + 0.1 b max|want| (elements with almost no weight are compared
+    on the scale of their projection)."""
+    import numpy as np
+    got = np.asarray(got, np.float64)
+    want = np.asarray(want, np.float64)
+    scale = np.abs(want) + 0.1 * np.max(np.abs(want))
+    return float(np.max(np.abs(got - want) / scale))
+
+
+def sample_elements(g, n, seed):
+    """(view, k, l) detector elements spread over views, columns and rows (every row window)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    v = rng.integers(0, g["n_views"], n)
+    k = rng.integers(g["nu"] // 6, g["nu"] - g["nu"] // 6, n)
+    l = (np.arange(n) * (g["nv"] - 1)) // max(n - 1, 1)
+    return [(int(a), int(b), int(c)) for a, b, c in zip(v, k, l)]
+
+
+def cpu_baseline_3d(g, x_host, p_gpu_item0, P, dev, target_s=12.0):
+    """The oracle on the host cores on a sample of the 3D workload, and the parity of the
+    timed kernels on it: the oracle's back projection of one view over a z-slab (timed:
+    updates/s), the GPU back projection of the same synthetic view against it, and sampled
+    detector elements of the timed forward (batch item 0) against the oracle's."""
+    import numpy as np
+    import torch
+    import oracle
+    import paper_2511_12235_gb300 as csm
+    p, iz0, iz1 = cpu_slab_sample(g, target_s)
+    t0 = time.perf_counter()
+    xs, n_upd = oracle.back_slab_3d(g, p, iz0, iz1, views=[0])
+    dt = time.perf_counter() - t0
+    g1 = dict(g)
+    g1["angles"] = g["angles"][:1].copy()
+    g1["n_views"] = 1
+    P1 = csm.Projector(g1, device=dev)
+    b = P1.back(torch.from_numpy(p).float().to(dev))[iz0:iz1].double().cpu().numpy()
+    P1.close()
+    back_err = elementwise_rel(b, xs)
+    els = sample_elements(g, 24, seed=3)
+    want = np.array([oracle.forward_element_3d(g, x_host, v, k, l) for v, k, l in els])
+    got = np.array([float(p_gpu_item0[v, l, k]) for v, k, l in els])
+    fwd_err = elementwise_rel(got, want)
+    return {"value": n_upd / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": "FP64 oracle back projection W^T p of view 0 over voxel slices %d..%d of %d "
+                      "(%d nonzero entries, %.1f s), p seeded uniform" % (iz0, iz1 - 1, g["nz"], n_upd, dt),
+            "back_parity_max_rel": back_err,
+            "forward_parity_max_rel": fwd_err,
+            "parity_note": "per sample |gpu - oracle| / (|oracle| + 0.1 max|oracle|): the back over the "
+                           "slab's %d voxels, the timed forward on %d sampled detector elements"
+                           % (xs.size, len(els))}
+
+
+def cpu_baseline_2d(P, x):
+    import numpy as np
+    import oracle
+    gq, xq, views, cores = cpu_oracle_leg(1, target_s=12.0)
+    n_sample = oracle.count_2d(gq, views=views)
+    t0 = time.perf_counter()
+    pq = oracle.forward_2d(gq, xq, views=views)
+    oracle.back_2d(gq, pq, views=views)
+    dt = time.perf_counter() - t0
+    # parity of the timed forward (batch item 0, the same phantom) on the sampled views
+    p_gpu = P.forward(x)[0].double().cpu().numpy()[views]
+    num = np.linalg.norm(p_gpu - pq, axis=1)
+    den = np.linalg.norm(pq, axis=1)
+    rel = float(np.max(num[den > 0] / den[den > 0]))
+    return {"value": 2.0 * n_sample / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "FP64 oracle fwd+back of 1 phantom over %d of 720 views (%d entries), %.1f s"
+                      % (len(views), n_sample, dt),
+            "forward_parity_max_rel_l2_per_view": rel}
 
 
 # ---------------------------------------------------------------------------------------
@@ -246,6 +385,7 @@ def run_ours(args, rank, world, local):
         dist.init_process_group("nccl", device_id=dev)
     try:
         import paper_2511_12235_gb300 as csm
+        from paper_2511_12235_gb300 import _capi  # noqa: F401  (loads the library)
     except ImportError:
         from paper_2511_12235_gb300 import build
         build.build()
@@ -261,9 +401,13 @@ def run_ours(args, rank, world, local):
     if g["dim"] == 2:
         xs_host = np.stack([synth.ellipse_phantom(g["nx"], s) for s in seeds]).astype(np.float32)
     else:
-        xs_host = np.stack([synth.ellipsoid_phantom(g["nx"], s, dtype=np.float32) for s in seeds])
+        xs_host = np.stack([synth.ellipsoid_phantom(g["nx"], s, dtype=np.float32, slab=8,
+                                                    workers=os.cpu_count() or 1) for s in seeds])
     x_zero_fraction = float((xs_host == 0).mean())
     x = torch.from_numpy(xs_host).to(dev).to(tdt)
+    # the same phantoms with no zero voxel: every entry of W contributes to the forward
+    x_dense = (torch.from_numpy(xs_host).to(dev) + 0.05).to(tdt)
+    peak = measure_alu_peak(dev, local)
     P = csm.Projector(g, device=dev)
     nnz = P.nnz()
     stream = torch.cuda.current_stream(dev)
@@ -298,9 +442,12 @@ def run_ours(args, rank, world, local):
     barrier()
     clk = clocks.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    p_item0 = p[0].float().cpu().numpy() if g["dim"] == 3 else None
 
     # --- per-kernel timing for the roofline: forward alone, back alone ------------------
-    def time_op(fn, n=5):
+    n_op = 3 if g["dim"] == 3 else 5
+
+    def time_op(fn, n=n_op):
         es = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
         for i in range(n):
             flush.fill_(float(i))
@@ -312,13 +459,16 @@ def run_ours(args, rank, world, local):
 
     t_fwd = time_op(lambda: P.forward(x, out=p))
     t_back = time_op(lambda: P.back(p, out=xb))
+    p_dense = torch.empty_like(p)
+    t_fwd_dense = time_op(lambda: P.forward(x_dense, out=p_dense))
 
     # --- end to end through the public API with host buffers ----------------------------
+    k_e2e = min(args.steps, 5)
     x_pin = x.cpu().pin_memory()
     out_pin = torch.empty((batch,) + P.vol_shape, dtype=tdt).pin_memory()
-    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ee = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(k_e2e)]
     barrier()
-    for i in range(args.steps):
+    for i in range(k_e2e):
         flush.fill_(float(i))
         ee[i][0].record(stream)
         xd = x_pin.to(dev, non_blocking=True)
@@ -328,63 +478,65 @@ def run_ours(args, rank, world, local):
         ee[i][1].record(stream)
     barrier()
     t_e2e = sum(a.elapsed_time(b) for a, b in ee)
+    del pp, r
 
-    t_ms, t_e2e, t_fwd, t_back = max_over_ranks([t_ms, t_e2e, t_fwd, t_back], world, dev)
+    t_ms, t_e2e, t_fwd, t_back, t_fwd_dense = max_over_ranks([t_ms, t_e2e, t_fwd, t_back, t_fwd_dense], world, dev)
 
     updates_per_step = 2.0 * nnz * batch * world
     value = updates_per_step * args.steps / (t_ms / 1e3) / 1e9
     # (voxel, view) pairs visited by the two projections, per second
     voxel_views = 2.0 * g["nx"] * g["ny"] * g["nz"] * g["n_views"] * batch * world * args.steps / (t_ms / 1e3) / 1e9
-    e2e_value = updates_per_step * args.steps / (t_e2e / 1e3) / 1e9
+    e2e_value = updates_per_step * k_e2e / (t_e2e / 1e3) / 1e9
+    dense_value = updates_per_step / ((t_fwd_dense + t_back) / 1e3) / 1e9
 
     # roofline of the dominant kernel (ALU bound: algorithmic flops / launch time)
     dom, t_dom = ("forward", t_fwd) if t_fwd >= t_back else ("back", t_back)
     fpe = FLOPS_PER_ENTRY_WEIGHT[g["dim"]]
     flops = nnz * (fpe + 2 * batch)
     achieved = flops / (t_dom / 1e3) / 1e12
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_alu_peak_tflops(sm_max)
+    fp64 = tdt == torch.float64
+    long_kernel = t_dom > 100.0
+    if fp64:
+        pk, which = peak["fp64_burst_tflops"], "FP64 FMA burst"
+    elif long_kernel:
+        pk, which = peak["fp32_sustained_tflops"], "FP32 FMA sustained"
+    else:
+        pk, which = peak["fp32_burst_tflops"], "FP32 FMA burst"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": sdt, "data": "synthetic",
         "config": {"workload": wl, "grid": [g["nx"], g["ny"]] + ([g["nz"]] if g["dim"] == 3 else []),
                    "views": g["n_views"], "detector": [g["nu"]] + ([g["nv"]] if g["dim"] == 3 else []),
+                   "s": g["s"], "sdd": g["sdd"],
                    "batch": batch, "nnz_per_item": nnz, "x_zero_fraction": round(x_zero_fraction, 4),
-                   "l2": "flushed before every timed step (512 MiB write, untimed)",
+                   "l2": "flushed before every timed step (512 MiB write, untimed); inputs larger than L2"
+                         if g["dim"] == 3 else "flushed before every timed step (512 MiB write, untimed)",
                    "step": "forward over all views + back projection of the batch"},
         "gpu_launches": 4 * args.steps,
         "gvoxel_views_per_s": voxel_views,
-        "kernels_ms": {"forward": t_fwd, "back": t_back},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": dram_traffic(wl, dom),
+        "kernels_ms": {"forward": t_fwd, "back": t_back, "forward_dense_input": t_fwd_dense},
+        "dense_input": {"value": dense_value, "unit": UNIT, "x_zero_fraction": 0.0,
+                        "note": "the same rate with the forward of the phantoms plus 0.05 (no zero voxel: "
+                                "every entry of W is evaluated and applied) and the timed back projection"},
+        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                     "frac": achieved / pk, "traffic": dram_traffic(wl, dom),
                      "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                     "peak_note": "FP32 FMA peak 152 SMs x 128 lanes x 2 x %.0f MHz (max SM clock); "
-                                  "algorithmic flops = nnz x (%d + 2 x batch)" % (sm_max, fpe)},
+                     "peak_note": "%s rate measured in this run by csm_fma_rate (of measured); algorithmic "
+                                  "flops = nnz x (%d + 2 x batch)" % (which, fpe)},
+        "alu_peak_measured": peak,
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_pin.numel() * 4),
-                "d2h_bytes_per_step": int(out_pin.numel() * 4)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_pin.numel() * x_pin.element_size()),
+                "d2h_bytes_per_step": int(out_pin.numel() * out_pin.element_size()), "steps": k_e2e,
+                "note": "Projector.forward/back from pinned host input to pinned host output, H2D and D2H "
+                        "inside the timed region"},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl == WORKLOAD:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and wl in ("cone3d_512", "fan2d_512"):
         try:
-            import oracle
-            gq, xq, views, cores = cpu_oracle_leg(1, target_s=12.0)
-            n_sample = oracle.count_2d(gq, views=views)
-            t0 = time.perf_counter()
-            pq = oracle.forward_2d(gq, xq, views=views)
-            oracle.back_2d(gq, pq, views=views)
-            dt = time.perf_counter() - t0
-            # parity of the timed forward (batch item 0, the same phantom) on the sampled views
-            p_gpu = P.forward(x)[0].double().cpu().numpy()[views]
-            num = np.linalg.norm(p_gpu - pq, axis=1)
-            den = np.linalg.norm(pq, axis=1)
-            rel = float(np.max(num[den > 0] / den[den > 0]))
-            line["cpu_baseline"] = {
-                "value": 2.0 * n_sample / dt / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": "FP64 oracle fwd+back of 1 phantom over %d of 720 views (%d entries), %.1f s"
-                          % (len(views), n_sample, dt),
-                "forward_parity_max_rel_l2_per_view": rel}
+            if g["dim"] == 3:
+                line["cpu_baseline"] = cpu_baseline_3d(g, xs_host[0].astype(np.float64), p_item0, P, dev)
+            else:
+                line["cpu_baseline"] = cpu_baseline_2d(P, x)
         except Exception as e:  # the baseline is reported, not required
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": None, "kind": "oracle",
                                     "sample": "failed: %s" % e}

@@ -149,20 +149,21 @@ def _ellipsoid_params(n: int, seed: int, n_ellipsoids: int):
 
 
 def ellipsoid_phantom(n: int, seed: int, n_ellipsoids: int = 10, dtype=np.float64,
-                      slab: int = 32) -> np.ndarray:
+                      slab: int = 32, workers: int = 1) -> np.ndarray:
     """A body ellipsoid and ``n_ellipsoids`` random ellipsoids on an n^3 grid of unit voxels
     centred at 0 ([nz][ny][nx]; R = n/2).
 
     Body: centre uniform in the ball of radius 0.05 R, semi-axes U[0.75, 0.92] R, value
     U[0.1, 0.3].  Inner ellipsoids: centre uniform in the ball of radius 0.7 R, semi-axes
     U[0.05, 0.35] R, value U[0, 1].  Uniformly random rotations.  Evaluated slab by slab to
-    bound memory.
+    bound memory (``workers`` threads share the slabs; the result does not depend on it).
     """
     params = _ellipsoid_params(n, seed, n_ellipsoids)
     xs = (np.arange(n) - n / 2.0 + 0.5)
     out = np.zeros((n, n, n), dtype=dtype)
     Y, X = np.meshgrid(xs, xs, indexing="ij")
-    for z0 in range(0, n, slab):
+
+    def one_slab(z0):
         zs = xs[z0:z0 + slab]
         Z = zs[:, None, None]
         acc = np.zeros((len(zs), n, n), dtype=np.float64)
@@ -174,6 +175,14 @@ def ellipsoid_phantom(n: int, seed: int, n_ellipsoids: int = 10, dtype=np.float6
                 q = q + (comp / ax[r]) ** 2
             acc[q <= 1.0] += val
         out[z0:z0 + slab] = acc
+
+    if workers > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(max_workers=workers) as ex:
+            list(ex.map(one_slab, range(0, n, slab)))
+    else:
+        for z0 in range(0, n, slab):
+            one_slab(z0)
     return out
 
 

@@ -8,14 +8,20 @@ import types
 import bench
 
 
-def test_reference_arm_json(monkeypatch):
+import pytest
+
+
+@pytest.mark.parametrize("workload", ["cone3d_512", "fan2d_512"])
+def test_reference_arm_json(monkeypatch, workload):
     leg = bench.cpu_oracle_leg
     monkeypatch.setattr(bench, "cpu_oracle_leg", lambda steps, target_s=15.0: leg(steps, target_s=1.0))
-    args = types.SimpleNamespace(steps=2, warmup=1)
+    monkeypatch.setattr(bench, "REFERENCE_TOTAL_S", 1.5)
+    args = types.SimpleNamespace(steps=2, warmup=1, workload=workload)
     out = io.StringIO()
     with contextlib.redirect_stdout(out):
         bench.run_reference(args, 0, 1)
     line = json.loads(out.getvalue().strip().splitlines()[-1])
+    assert line["config"]["workload"].startswith(workload)
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                 "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in line, key

@@ -180,6 +180,35 @@ def test_fan512_batch16_sampled_views(csm):
     assert rel(bx, oracle.back_2d(gs, ref_p)) < FP32_TOL
 
 
+def assert_elementwise(got, want, tol, what=""):
+    """Every sample: |got - want| <= tol |want| + 0.1 tol max|want| (relative error per
+    element, floored at a tenth of the largest value for elements of almost no weight)."""
+    got = np.asarray(got, np.float64).ravel()
+    want = np.asarray(want, np.float64).ravel()
+    bound = tol * (np.abs(want) + 0.1 * np.max(np.abs(want)))
+    bad = np.abs(got - want) > bound
+    assert not bad.any(), (what, int(bad.sum()), float(np.max(np.abs(got - want) / bound)) * tol)
+
+
+def test_fan512_back_all_views_elementwise(csm):
+    """The back projection over all 720 views in the benchmark's launch configuration
+    (batch 16), pixel by pixel against the oracle, for two batch items; and the forward of
+    the whole sinogram element by element on 24 views of one phantom."""
+    g = synth.config("fan2d_512")
+    rng = np.random.default_rng(21)
+    ps = rng.uniform(size=(16, 720, 768))
+    P = csm.Projector(g)
+    b = P.back(torch.from_numpy(ps).float().cuda()).cpu().numpy()
+    for bi in (0, 13):
+        assert_elementwise(b[bi], oracle.back_2d(g, ps[bi]), FP32_TOL, "back item %d" % bi)
+    xs = np.stack([synth.ellipse_phantom(512, s) for s in range(16)])
+    p = P.forward(torch.from_numpy(xs).float().cuda()).cpu().numpy()
+    views = np.arange(7, 720, 30)
+    ref = oracle.forward_2d(g, xs[9], views=views)
+    for i, v in enumerate(views):
+        assert_elementwise(p[9, v], ref[i], FP32_TOL, "forward view %d" % v)
+
+
 def test_batch_invariance(csm):
     """A batch item's projections do not depend on the other items of its batch or on the
     batch size (the 16-, 8-, 2- and 1-item kernels give bit-identical results)."""
