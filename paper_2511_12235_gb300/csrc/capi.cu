@@ -39,6 +39,9 @@ Geo make_geo(const csm_geom_s* g) {
     o.v0 = (float)o.v0_d; o.x0 = (float)o.x0_d; o.y0 = (float)o.y0_d; o.z0 = (float)o.z0_d;
     o.idu_d = 1.0 / o.du_d; o.idv_d = 1.0 / o.dv_d; o.ic_d = 1.0 / o.c_d;
     o.idu = (float)o.idu_d; o.idv = (float)o.idv_d; o.ic = (float)o.ic_d;
+    o.qmax_d = std::max(fabs(o.v0_d), fabs(o.v0_d + g->nv * o.dv_d)) / o.sdd_d;
+    o.dq_d = o.dv_d / o.sdd_d;
+    o.qmax = (float)o.qmax_d; o.dq = (float)o.dq_d;
     o.axis_sigma = g->t.axis_sigma; o.cs_f = g->t.cs_f; o.cs_d = g->t.cs_d;
     o.line_fx = g->t.line_fx; o.line_d = g->t.line_d; o.inv_f = g->t.inv_f; o.inv_d = g->t.inv_d;
     o.wrange = g->t.wrange; o.rowq_f = g->t.rowq_f; o.rowq_d = g->t.rowq_d;

@@ -77,6 +77,10 @@ struct Geo {
     // reciprocals 1/du, 1/dv, 1/c (rounded from FP64), so that no kernel divides by them
     float idu, idv, ic;
     double idu_d, idv_d, ic_d;
+    // row planes: largest |q_l| = |v_l| / sdd over the detector's row corners, and the step
+    // dq = dv / sdd between neighbouring corners (3D)
+    float qmax, dq;
+    double qmax_d, dq_d;
     const int* axis_sigma;
     const float* cs_f;
     const double* cs_d;

@@ -41,7 +41,8 @@ size_t workspace_3d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
     const size_t es = dbl ? 8 : 4;
     const size_t nb = chunk3(batch);
     const size_t vol = al256((size_t)g->nx * g->ny * g->nz * nb * es);
-    const size_t sino = al256((size_t)g->n_views * g->nv * g->nu * nb * es);
+    // back: the differenced sinogram, 4 values per (view, corner 0..nu, plane slot 0..nv+1)
+    const size_t sino = al256((size_t)g->n_views * (g->nu + 1) * (g->nv + 2) * 4 * nb * es);
     if (op == 0) return 2 * vol;   // the volume in both walk layouts
     return sino;
 }
@@ -95,6 +96,8 @@ template <> struct G3<float> {
     static __device__ __forceinline__ float ic(const Geo& g) { return g.ic; }
     static __device__ __forceinline__ float cs(const Geo& g, int v, int i) { return g.cs_f[2 * v + i]; }
     static __device__ __forceinline__ float q(const Geo& g, int l) { return g.rowq_f[l]; }
+    static __device__ __forceinline__ float qmax(const Geo& g) { return g.qmax; }
+    static __device__ __forceinline__ float dq(const Geo& g) { return g.dq; }
     static __device__ __forceinline__ float div(float x, float y) { return __fdividef(x, y); }
     static constexpr float eps = 1e-3f;
 };
@@ -116,6 +119,8 @@ template <> struct G3<double> {
     static __device__ __forceinline__ double ic(const Geo& g) { return g.ic_d; }
     static __device__ __forceinline__ double cs(const Geo& g, int v, int i) { return g.cs_d[2 * v + i]; }
     static __device__ __forceinline__ double q(const Geo& g, int l) { return g.rowq_d[l]; }
+    static __device__ __forceinline__ double qmax(const Geo& g) { return g.qmax_d; }
+    static __device__ __forceinline__ double dq(const Geo& g) { return g.dq_d; }
     static __device__ __forceinline__ double div(double x, double y) { return x / y; }
     static constexpr double eps = 1e-9;
 };
@@ -156,34 +161,86 @@ __device__ __forceinline__ double plane_height(const Geo& g, int l, int iz, doub
 }
 
 // ---------------------------------------------------------------------------------------
-// Layouts.  Forward reads x as xs0[ix][q][iz][iy][VW] (walk x) / xs1[iy][q][iz][ix][VW]
-// (walk y): lanes handle neighbouring elements, i.e. neighbouring cross cells.  Back reads
-// p as ps[v][q][l][k][VW].
+// Layouts.  The forward deals the voxels of one column to the lanes of a warp, so it reads x
+// with z innermost: xs0[ix][iy][iz][NB] (walk x) / xs1[iy][ix][iz][NB] (walk y).  The back
+// projection deals neighbouring voxels of a column to neighbouring lanes, whose rows of the
+// detector are neighbours too, so it reads p with the rows innermost: ps[v][k][l][NB].
+// Both copies are made by 32 x 32 tiled transposes through shared memory (coalesced reads
+// and writes).
 // ---------------------------------------------------------------------------------------
 template <typename T, int NB>
-__global__ void prep_vol_3d(const void* __restrict__ x, int xdt, int B, int b_off, int nx, int ny, int nz,
-                            T* __restrict__ xs0, T* __restrict__ xs1) {
+__global__ void __launch_bounds__(256) prep_vol_3d(const void* __restrict__ x, int xdt, int B, int b_off, int nx,
+                                                   int ny, int nz, T* __restrict__ xs0, T* __restrict__ xs1) {
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, iy = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const size_t n = (size_t)nx * ny * nz;
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int ix = (int)(i % nx), iy = (int)((i / nx) % ny), iz = (int)(i / ((size_t)nx * ny));
-#pragma unroll
     for (int bb = 0; bb < NB; ++bb) {
         const int b = b_off + bb;
-        const T val = b < B ? load_any3<T>(x, (size_t)b * n + i, xdt) : T(0);
-        xs0[((((size_t)ix) * nz + iz) * ny + iy) * NB + bb] = val;
-        xs1[((((size_t)iy) * nz + iz) * nx + ix) * NB + bb] = val;
+        for (int j = ty; j < 32; j += 8) {
+            const int ix = x0 + tx, iz = z0 + j;
+            T val = T(0);
+            if (ix < nx && iz < nz && b < B) val = load_any3<T>(x, (size_t)b * n + ((size_t)iz * ny + iy) * nx + ix, xdt);
+            tile[j][tx] = val;
+        }
+        __syncthreads();
+        for (int j = ty; j < 32; j += 8) {
+            const int ix = x0 + j, iz = z0 + tx;
+            if (ix < nx && iz < nz) {
+                const T val = tile[tx][j];
+                xs0[(((size_t)ix * ny + iy) * nz + iz) * NB + bb] = val;
+                xs1[(((size_t)iy * nx + ix) * nz + iz) * NB + bb] = val;
+            }
+        }
+        __syncthreads();
     }
 }
 
+// The back projection reads, per view, corner / element column i = 0 .. nu and plane slot
+// r = 0 .. nv + 1 (p = 0 outside the detector), the four values
+//     .x  DD(i, r) = Dc(i, r - 1) - Dc(i, r)      Dc(i, l) = p(i - 1, l) - p(i, l)
+//     .y  Dc(i, r - 1)
+//     .z  Dy(i, r) = p(i, r - 1) - p(i, r)
+//     .w  p(i, r - 1)
+// stored as q[v][i][r][component][NB] (the sums by parts of the voxel_back_fast form).  Each
+// block differences a 32 x 32 tile of p held in shared memory with a one-element halo.
 template <typename T, int NB>
-__global__ void prep_sino_3d(const void* __restrict__ p, int pdt, int B, int b_off, size_t n, T* __restrict__ ps) {
-    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-#pragma unroll
+__global__ void __launch_bounds__(256) prep_diff_3d(const void* __restrict__ p, int pdt, int B, int b_off, int nu,
+                                                    int nv, T* __restrict__ q) {
+    __shared__ T tile[34][34];   // p(i0 - 1 + a, r0 - 1 + b) at tile[b][a], a, b in [0, 33]
+    const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, v = blockIdx.z;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const size_t plane = (size_t)nu * nv;
+    const size_t nvw = plane * gridDim.z;
+    const size_t slots = (size_t)(nu + 1) * (nv + 2);
     for (int bb = 0; bb < NB; ++bb) {
         const int b = b_off + bb;
-        ps[i * NB + bb] = b < B ? load_any3<T>(p, (size_t)b * n + i, pdt) : T(0);
+        for (int e = ty * 32 + tx; e < 34 * 34; e += 256) {
+            const int ta = e % 34, tb = e / 34;
+            const int k = i0 - 1 + ta, l = r0 - 1 + tb;
+            T val = T(0);
+            if (k >= 0 && k < nu && l >= 0 && l < nv && b < B)
+                val = load_any3<T>(p, (size_t)b * nvw + (size_t)v * plane + (size_t)l * nu + k, pdt);
+            tile[tb][ta] = val;
+        }
+        __syncthreads();
+        // thread (tx, ty): plane slot r = r0 + tx (coalesced writes along r), corners i0 + ty + 8 j
+        const int r = r0 + tx;
+        for (int j = ty; j < 32; j += 8) {
+            const int i = i0 + j;
+            if (i <= nu && r <= nv + 1) {
+                // tile coordinates of p(i - 1, r - 1): (a, b) = (j, tx)
+                const T pm1 = tile[tx][j], p0m1 = tile[tx][j + 1];     // p(i-1, r-1), p(i, r-1)
+                const T pm0 = tile[tx + 1][j], p00 = tile[tx + 1][j + 1];  // p(i-1, r),   p(i, r)
+                const T dcm = pm1 - p0m1, dc0 = pm0 - p00;
+                T* dst = q + (((size_t)v * slots + (size_t)i * (nv + 2) + r) * 4) * NB + bb;
+                dst[0] = dcm - dc0;
+                dst[NB] = dcm;
+                dst[2 * NB] = p0m1 - p00;
+                dst[3 * NB] = p0m1;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -219,7 +276,7 @@ struct __align__(16) AtomP {
     T cf[7][4];   // per piece: M and its first three derivatives / n! at the piece's base
     T tau[6];     // sorted vertex depths
     T A;          // area
-    T pad;
+    T M1;         // first moment of the depth t' over the atom (integral of t' dA)
 };
 
 template <typename T> struct Cf4;
@@ -302,14 +359,19 @@ __device__ __forceinline__ void build_piece(AtomP<T>& P, int p, T lam0, T lam1, 
     if (p == 1) {
         P.cf[0][0] = k * c0; P.cf[0][1] = k * c1; P.cf[0][2] = T(0); P.cf[0][3] = T(0);
         P.cf[6][0] = T(0); P.cf[6][1] = T(0); P.cf[6][2] = T(0); P.cf[6][3] = T(0);
-        T a2 = T(0);
+        // area and first moment of t' by a fan of triangles from the cell centre (where t' = 0):
+        // each edge's triangle has signed area cr/2 and mean t' (TP_i + TP_j)/3
+        T a2 = T(0), m6 = T(0);
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
             const int j = (i + 1) % 6;
-            a2 += XI[i] * ET[j] - XI[j] * ET[i];
+            const T cr = (XI[i] - T(0.5)) * (ET[j] - T(0.5)) - (XI[j] - T(0.5)) * (ET[i] - T(0.5));
+            a2 += cr;
+            m6 += cr * (TP[i] + TP[j]);
             P.tau[i] = ts[i];
         }
         P.A = T(0.5) * a2 * hw * hc;
+        P.M1 = m6 * hw * hc * T(1.0 / 6.0);
     }
 }
 
@@ -358,6 +420,7 @@ struct ColumnView {
     T tmin_w, tmax_w;                   // world depth range of the column
     T margin_c;                         // largest |t'| in the cell, in units of the voxel height c
     T dh, dl;                           // centre depth / c as a pair (column_depth)
+    int fast;                           // planes meet voxel faces one at a time (see face_kink)
 };
 
 // Classification of the corner lines of one column's footprint, computed cooperatively by
@@ -395,6 +458,15 @@ __device__ __forceinline__ void column_view(const Geo& g, int v, int ix, int iy,
     cv.tmax_w = tmax;
     column_depth(g, v, ix, iy, cv.dh, cv.dl);
     cv.margin_c = T(0.5) * (fabs(a * cs) + fabs(b * sn)) * G3<T>::ic(g);
+    {
+        // A row plane dips below / rises above a horizontal voxel face inside the cell only
+        // within m = |q| margin_c (units of c) of it.  When 2 m is below the smallest spacing
+        // of neighbouring planes at this column (dq t_min / c) and m < 1/2, at most one plane
+        // does so at each face and no plane does so at both faces of one voxel.
+        const T m = G3<T>::qmax(g) * cv.margin_c;
+        const T pitch = G3<T>::dq(g) * tmin * G3<T>::ic(g);
+        cv.fast = (T(2) * m + T(0.02) < pitch) && (m < T(0.45));
+    }
     const T idu = G3<T>::idu(g);
     T f0 = floor((umin - G3<T>::u0(g)) * idu - G3<T>::eps), f1 = floor((umax - G3<T>::u0(g)) * idu + G3<T>::eps);
     cv.ok = 0;
@@ -543,14 +615,200 @@ __device__ __forceinline__ void voxel_entries(const Geo& g, int v, int ix, int i
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Faces and kinks (the fast form of Phi).  With y = g + q t' the plane's height above the
+// voxel's bottom face,  clamp(y, 0, c) = y + relu(-y) - relu(y - c).  A plane whose height
+// range over the cell (h +- m in units of c, m = |q| margin_c) lies inside (0, 1) therefore has
+// the linear Phi = g A + q M1 (A the atom's area, M1 its first moment of t'), a plane below
+// the voxel Phi = 0 and one above Phi = c A.  Only a plane within m of a face needs the tail
+// moments, and its correction is one number per (face, atom): the volume on the minority side
+// of the plane next to the face,
+//     K_f = integral over the atom of relu(s (g_f + q t')),   s = -sign(g_f)   (g_f: the
+// plane's height above face f at the cell centre),
+// which enters the voxel above the face with + and the voxel below it with -:
+//     Phi(plane, voxel iz) = base(h) + K_iz - K_{iz+1},
+//     base(h) = 0 (h < 0), g A + q M1 (0 <= h < 1), c A (h >= 1),  h at the cell centre.
+// With relu(q (t' - x)), x = -g / q, one table evaluation gives K: |q| M(x) or |q| H(x) with
+// the head moment H(x) = integral of relu(x - t') = x A - M1 + M(x).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T kink_tail(const AtomP<T>& P, T gw, T q, T iq, bool below) {
+    T tau[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) tau[i] = P.tau[i];
+    const T x = -gw * (q < T(0) ? -iq : iq);
+    const bool use_m = below == (q > T(0));
+    const T mv = eval_m<T>(P, tau, x);
+    return fabs(q) * (use_m ? mv : mv + (x * P.A - P.M1));
+}
+
+// The plane (if any) that meets the bottom face of voxel iz inside the cell, and its K for the
+// whole-cell atom (slot 0) and each crossing line's atom (slots 1 .. ng), written to kslot.
+// Returns the plane's index, or -1; ra receives the first plane whose height at the cell
+// centre is at or above the face (0 .. nv + 1).  Requires cv.fast.
+template <typename T>
+__device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
+                                         const AtomP<T>& full, T* kslot, int& ra) {
+    // nearest planes: q t_c / c = iz - nz/2 at the face, planes q_r = (v0 + r dv) / sdd
+    const T fz = T(iz) - T(0.5) * T(g.nz);
+    const T qf = G3<T>::div(fz, cv.dh + cv.dl);
+    const T rf = (qf * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
+    const T rfl = floor(rf);
+    // the two planes around the face (plane heights increase with r)
+    const int r0 = rfl < T(-1) ? -1 : (rfl > T(g.nv) ? g.nv : (int)rfl);
+    int rb = -1;
+    T hb = T(0), qb = T(0), iqb = T(0);
+    ra = r0 + 1;
+#pragma unroll
+    for (int c2 = 0; c2 < 2; ++c2) {
+        const int r = r0 + c2;
+        if (r >= 0 && r <= g.nv) {
+            T q, iq;
+            const T h = plane_height(g, r, iz, cv.dh, cv.dl, q, iq);
+            if (c2 == 0 && h >= T(0)) ra = r0;
+            if (fabs(h) < fabs(q) * cv.margin_c) { rb = r; hb = h; qb = q; iqb = iq; }
+        }
+    }
+    const int na = cv.ng + 1;
+    const T gw = hb * G3<T>::c(g);
+#pragma unroll
+    for (int j = 0; j <= kMaxG; ++j) {
+        if (j < na) {
+            T kv = T(0);
+            if (rb >= 0) kv = kink_tail<T>(j == 0 ? full : atoms[j - 1], gw, qb, iqb, hb < T(0));
+            kslot[j] = kv;
+        }
+    }
+    return rb;
+}
+
+// Back projection of one voxel for one view in the fast form, by sums by parts over the
+// detector's columns and rows.  With Phi_i(r) the volume of the voxel below row plane r and
+// below corner line i (lines left of the footprint: empty or the whole cell, right of it:
+// the other), the voxel's value  sum_{k,l} W(k, l) p(k, l)  equals
+//     sigma sum_i sum_r Phi_i(r) DD(i, r)      (p = 0 outside the detector),
+// Phi_i(r) = 0 for planes below the voxel and c A_i for planes above it, and the lines of
+// the whole-cell type telescope into the footprint's boundary column b.  What remains per
+// line: the planes whose centre lies in the voxel (ra .. rtop - 1) with the linear Phi, the
+// first plane above (c A_i Dc(i, rtop - 1)), and the two face corrections K.  q: this view's
+// differenced projections (prep_diff_3d).
+template <typename T, int NB>
+__device__ __forceinline__ void voxel_back_fast(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
+                                                const AtomP<T>& full, const T* __restrict__ qv, int ra, int rtop,
+                                                int rb, const T* kb, int rt, const T* kt, T (&sum)[NB]) {
+    const int ng = cv.ng;
+    const int ns = g.nv + 2;
+    const T c = G3<T>::c(g);
+    // boundary column of the whole-cell lines and its sign after telescoping
+    const int bcol = cv.sigma > 0 ? cv.k_first + ng : cv.k_first;
+    const bool bok = bcol >= 0 && bcol < g.nu;
+    const T sb = cv.sigma > 0 ? T(1) : T(-1);
+    const int k1 = cv.k_first + 1;   // first crossing line
+    auto at = [&](int i, int r, int comp) { return qv + (((size_t)i * ns + r) * 4 + comp) * NB; };
+    T acc[NB];
+#pragma unroll
+    for (int n = 0; n < NB; ++n) acc[n] = T(0);
+    const int rlo = ra < 0 ? 0 : ra, rhi = rtop > g.nv + 1 ? g.nv + 1 : rtop;
+#pragma unroll 1
+    for (int r = rlo; r < rhi; ++r) {   // planes with their centre inside the voxel (r <= nv)
+        T q, iq;
+        const T gw = plane_height(g, r, iz, cv.dh, cv.dl, q, iq) * c;
+#pragma unroll
+        for (int j = 0; j < kMaxG; ++j) {
+            if (j < ng) {
+                const AtomP<T>& P = atoms[j];
+                fma_vec<T, NB>(acc, gw * P.A + q * P.M1, at(k1 + j, r, 0));
+            }
+        }
+        if (bok) fma_vec<T, NB>(acc, sb * gw * full.A, at(bcol, r, 2));
+    }
+    // the first plane above the voxel: the telescoped sum of every plane above it
+#pragma unroll
+    for (int j = 0; j < kMaxG; ++j)
+        if (j < ng) fma_vec<T, NB>(acc, c * atoms[j].A, at(k1 + j, rhi, 1));
+    if (bok) fma_vec<T, NB>(acc, sb * c * full.A, at(bcol, rhi, 3));
+    // face corrections
+    if (rb >= 0) {
+#pragma unroll
+        for (int j = 0; j < kMaxG; ++j)
+            if (j < ng) fma_vec<T, NB>(acc, kb[j + 1], at(k1 + j, rb, 0));
+        if (bok) fma_vec<T, NB>(acc, sb * kb[0], at(bcol, rb, 2));
+    }
+    if (rt >= 0) {
+#pragma unroll
+        for (int j = 0; j < kMaxG; ++j)
+            if (j < ng) fma_vec<T, NB>(acc, -kt[j + 1], at(k1 + j, rt, 0));
+        if (bok) fma_vec<T, NB>(acc, -sb * kt[0], at(bcol, rt, 2));
+    }
+    const T sg = cv.sigma > 0 ? T(1) : T(-1);
+#pragma unroll
+    for (int n = 0; n < NB; ++n) sum[n] = sg * acc[n];
+}
+
+// voxel_entries with the fast form of Phi: rb / kb the plane meeting the voxel's bottom face and
+// its K per atom, rt / kt the same for the top face (from the voxel above).
+template <typename T, typename Sink>
+__device__ __forceinline__ void voxel_entries_fast(const Geo& g, int ix, int iy, int iz, const ColumnView<T>& cv,
+                                                   const AtomP<T>* atoms, const AtomP<T>& full, int rb,
+                                                   const T* kb, int rt, const T* kt, Sink& sink) {
+    const T c = G3<T>::c(g);
+    const T z0w = G3<T>::z0(g) + iz * c;
+    int l0, l1;
+    if (!voxel_rows<T>(g, z0w, z0w + c, cv.tmin_w, cv.tmax_w, l0, l1)) return;
+    const int ng = cv.ng, na = ng + 1;
+    T pc[kMaxG + 1], pp[kMaxG + 1];
+#pragma unroll
+    for (int j = 0; j <= kMaxG; ++j) pp[j] = T(0);
+#pragma unroll 1
+    for (int r = l0; r <= l1 + 1; ++r) {
+        T q, iq;
+        const T h = plane_height(g, r, iz, cv.dh, cv.dl, q, iq);   // above the voxel bottom, units of c
+        const T gw = h * c;
+        const int cls = h < T(0) ? 0 : (h >= T(1) ? 2 : 1);
+        const bool on_b = r == rb, on_t = r == rt;
+#pragma unroll
+        for (int j = 0; j <= kMaxG; ++j) {
+            if (j < na) {
+                const AtomP<T>& P = j == 0 ? full : atoms[j - 1];
+                T v = cls == 0 ? T(0) : (cls == 2 ? c * P.A : gw * P.A + q * P.M1);
+                if (on_b) v += kb[j];
+                if (on_t) v -= kt[j];
+                pc[j] = v;
+            } else {
+                pc[j] = T(0);
+            }
+        }
+        if (r > l0) {
+            const int l = r - 1;
+            const T sf = pc[0] - pp[0];
+            T prevS = cv.sigma > 0 ? T(0) : sf;
+#pragma unroll
+            for (int j = 0; j <= kMaxG; ++j) {
+                if (j <= ng) {
+                    const T S = j < ng ? pc[j < kMaxG ? j + 1 : kMaxG] - pp[j < kMaxG ? j + 1 : kMaxG] : (cv.sigma > 0 ? sf : T(0));
+                    const int k = cv.k_first + j;
+                    const T wt = cv.sigma > 0 ? S - prevS : prevS - S;
+                    if ((cv.kin || (k >= 0 && k < g.nu)) && wt != T(0)) sink.add(k, l, wt);
+                    prevS = S;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j <= kMaxG; ++j) pp[j] = pc[j];
+    }
+}
+
+// Per-warp shared slots of the face corrections: one row of kKs values per lane.
+constexpr int kKs = kMaxG + 3;   // 9: rows of neighbouring lanes fall in different banks
+
 // Sink of the back projection: W p gathered from this view's projections.
 template <typename T, int NB>
 struct GatherSink {
-    const T* pv;        // this view's projections, [nv][nu][NB]
-    int nu;
+    const T* pv;        // this view's differenced projections (prep_diff_3d); p(k, l) is the .w
+    int nv;             // value at slot (k, l + 1)
     T sum[NB];
     __device__ __forceinline__ void add(int k, int l, T wt) {
-        fma_vec<T, NB>(sum, wt, pv + (size_t)(l * nu + k) * NB);
+        fma_vec<T, NB>(sum, wt, pv + ((size_t)(k * (nv + 2) + l + 1) * 4 + 3) * NB);
     }
 };
 
@@ -571,12 +829,14 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
                                                       int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
     __shared__ T acc_s[BW][NB * ZW];
+    __shared__ T ks_s[BW][32 * kKs];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;                       // whole warp leaves together
     const int ix = col % g.nx, iy = col / g.nx;
     const int zb = blockIdx.y * ZW, ze = min(zb + ZW, g.nz);
     AtomP<T>* atoms = atoms_s[wid];
+    T* ks = ks_s[wid];
     T* acc = acc_s[wid];                                  // acc[b * ZW + (iz - zb)]
     for (int i = lane; i < NB * ZW; i += 32) acc[i] = T(0);
     for (int v = 0; v < g.n_views; ++v) {
@@ -592,14 +852,34 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
         column_atoms<T>(g, v, ix, iy, cv, lane, atoms);
         __syncwarp();
         GatherSink<T, NB> sink;
-        sink.pv = ps + (size_t)v * g.nv * g.nu * NB;
-        sink.nu = g.nu;
-        for (int iz = z0 + lane; iz <= z1; iz += 32) {
+        sink.pv = ps + (size_t)v * (g.nu + 1) * (g.nv + 2) * 4 * NB;
+        sink.nv = g.nv;
+        if (cv.fast) {
+            // 31 voxels per pass; lane 31 finds the face above the last of them
+            for (int zc = z0; zc <= z1; zc += 31) {
+                const int iz = zc + lane;
+                int ra = 0;
+                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                __syncwarp();
+                const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
+                const int rtop = __shfl_down_sync(0xffffffffu, ra, 1);
+                if (lane < 31 && iz <= z1) {
+                    T vs[NB];
+                    voxel_back_fast<T, NB>(g, iz, cv, atoms, atoms[kMaxG], sink.pv, ra, rtop, rb, ks + lane * kKs, rt,
+                                           ks + (lane + 1) * kKs, vs);
 #pragma unroll
-            for (int i = 0; i < NB; ++i) sink.sum[i] = T(0);
-            voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
+                    for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += vs[i];
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int iz = z0 + lane; iz <= z1; iz += 32) {
 #pragma unroll
-            for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sink.sum[i];
+                for (int i = 0; i < NB; ++i) sink.sum[i] = T(0);
+                voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
+#pragma unroll
+                for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += sink.sum[i];
+            }
         }
     }
     __syncwarp();
@@ -652,6 +932,7 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
                                                      const T* __restrict__ xs1, void* __restrict__ p, int pdt,
                                                      int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[FW][kMaxG + 1];
+    __shared__ T ks_s[FW][32 * kKs];
     extern __shared__ __align__(16) unsigned char fwd_dyn[];   // [FW][KW][rw][NB] sums
     using L = typename LineOf<T>::type;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -663,6 +944,7 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
     T* rows = reinterpret_cast<T*>(fwd_dyn) + (size_t)wid * KW * rw * NB;   // [(k - kg) * rw + row][NB]
     for (int i = lane; i < KW * rw * NB; i += 32) rows[i] = T(0);
     AtomP<T>* atoms = atoms_s[wid];
+    T* ks = ks_s[wid];
     const int axis = g.axis_sigma[2 * v];
     const int nc = axis == 0 ? g.ny : g.nx;
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
@@ -706,7 +988,7 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             if (zhi < T(0) || zlo > T(g.nz - 1)) continue;
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
-            const T* xcol = xs + ((size_t)w * g.nz) * nc * NB + (size_t)cc * NB;
+            const T* xcol = xs + ((size_t)w * nc + cc) * g.nz * NB;
             // cells whose voxels in reach are all zero add nothing: skip them before any table
             // is built
             bool nzv = false;
@@ -714,7 +996,7 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
                 const int iz = zb + lane;
                 if (iz <= izhi) {
 #pragma unroll
-                    for (int i = 0; i < NB; ++i) nzv |= __ldg(xcol + (size_t)iz * nc * NB + i) != T(0);
+                    for (int i = 0; i < NB; ++i) nzv |= __ldg(xcol + (size_t)iz * NB + i) != T(0);
                 }
             }
             if (!__any_sync(0xffffffffu, nzv)) continue;
@@ -724,6 +1006,35 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
                 column_piece<T>(g, v, ix, iy, cv, i, it - 5 * i + 1, atoms[i]);
             }
             __syncwarp();
+            if (cv.fast) {
+                // 31 voxels per pass; lane 31 finds the face above the last of them.  A face's
+                // correction is needed only when the voxel above or below it is nonzero.
+                for (int zc = izlo; zc <= izhi; zc += 31) {
+                    const int iz = zc + lane;
+                    T xv[NB];
+                    bool own = false;
+#pragma unroll
+                    for (int i = 0; i < NB; ++i) {
+                        xv[i] = (lane < 31 && iz <= izhi) ? __ldg(xcol + (size_t)iz * NB + i) : T(0);
+                        own |= xv[i] != T(0);
+                    }
+                    const bool below = __shfl_up_sync(0xffffffffu, own, 1);
+                    const bool need = own || (lane > 0 && below);
+                    int ra = 0;
+                    const int rb = (need && iz <= izhi + 1) ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                    __syncwarp();
+                    const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
+                    if (own) {
+                        RowSink<T, NB> sink{rows, rw, kg, nk, L0, nrow};
+#pragma unroll
+                        for (int i = 0; i < NB; ++i) sink.xv[i] = xv[i];
+                        voxel_entries_fast<T>(g, ix, iy, iz, cv, atoms, atoms[kMaxG], rb, ks + lane * kKs, rt,
+                                              ks + (lane + 1) * kKs, sink);
+                    }
+                    __syncwarp();
+                }
+                continue;
+            }
             for (int zb = izlo; zb <= izhi; zb += 32) {
                 const int iz = zb + lane;
                 if (iz > izhi) continue;
@@ -731,7 +1042,7 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
                 bool any = false;
 #pragma unroll
                 for (int i = 0; i < NB; ++i) {
-                    xv[i] = __ldg(xcol + (size_t)iz * nc * NB + i);
+                    xv[i] = __ldg(xcol + (size_t)iz * NB + i);
                     any |= xv[i] != T(0);
                 }
                 if (!any) continue;
@@ -767,12 +1078,14 @@ struct CountSink {
 
 __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long long* counter) {
     __shared__ AtomP<float> atoms_s[BW][kMaxG + 1];
+    __shared__ float ks_s[BW][32 * kKs];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;
     const int ix = col % g.nx, iy = col / g.nx;
     const int zb = blockIdx.y * ZWN, ze = min(zb + ZWN, g.nz);
     AtomP<float>* atoms = atoms_s[wid];
+    float* ks = ks_s[wid];
     const float thr = 1e-6f * g.a * g.b * g.c;
     unsigned long long cnt = 0;
     for (int v = 0; v < g.n_views; ++v) {
@@ -788,8 +1101,22 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
         column_atoms<float>(g, v, ix, iy, cv, lane, atoms);
         __syncwarp();
         CountSink sink{thr, 0ull};
-        for (int iz = z0 + lane; iz <= z1; iz += 32)
-            voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
+        if (cv.fast) {
+            for (int zc = z0; zc <= z1; zc += 31) {
+                const int iz = zc + lane;
+                int ra = 0;
+                const int rb = iz <= z1 + 1 ? face_kink<float>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                __syncwarp();
+                const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
+                if (lane < 31 && iz <= z1)
+                    voxel_entries_fast<float>(g, ix, iy, iz, cv, atoms, atoms[kMaxG], rb, ks + lane * kKs, rt,
+                                              ks + (lane + 1) * kKs, sink);
+                __syncwarp();
+            }
+        } else {
+            for (int iz = z0 + lane; iz <= z1; iz += 32)
+                voxel_entries<float>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
+        }
         cnt += sink.n;
     }
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
@@ -833,8 +1160,8 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     T* xs1 = (T*)((char*)ws + half);
     const bool wide = (size_t)((gh->nu + 7) / 8) * gh->n_views >= 16384;
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
-        prep_vol_3d<T, NB><<<(unsigned)((nvox + 255) / 256), 256, 0, st>>>(x, (int)xdt, (int)batch, (int)b0,
-                                                                          gh->nx, gh->ny, gh->nz, xs0, xs1);
+        dim3 tb(32, 8), tg((gh->nx + 31) / 32, (gh->nz + 31) / 32, gh->ny);
+        prep_vol_3d<T, NB><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, gh->nz, xs0, xs1);
         csm_status e = wide ? launch_fwd3<T, NB, 8>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st)
                             : launch_fwd3<T, NB, 4>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st);
         if (e != CSM_OK) return e;
@@ -842,11 +1169,15 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     return CSM_OK;
 }
 
-// Window height of the back projection: the largest of 256 (FP32 only), 128, 64 that is not
-// taller than the grid and still leaves one warp per SM lane group (152 SMs x 32 warps).
-static int back_window(const csm_geom_s* g, bool dbl) {
+// Window height of the back projection: the largest of 512 / 256 / 128 / 64 voxels (at most
+// 512 voxel sums per warp in shared memory: NB x ZW <= 512; 128 in FP64) that is not much
+// taller than the grid and still leaves one warp per SM lane group (152 SMs x 32 warps).  A
+// taller window shares a column's per-view set-up (corner classification, atom tables) among
+// more voxels.
+static int back_window(const csm_geom_s* g, bool dbl, int nb) {
     const size_t ncol = (size_t)g->nx * g->ny;
-    for (int zw = dbl ? 128 : 256; zw > 64; zw >>= 1)
+    const int top = dbl ? 128 : 512 / nb;
+    for (int zw = top; zw > 64; zw >>= 1)
         if (g->nz > zw / 2 && ncol * (size_t)((g->nz + zw - 1) / zw) >= 152 * 32) return zw;
     return 64;
 }
@@ -867,12 +1198,14 @@ static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_
     const Geo g = make_geo(gh);
     T* ps = (T*)ws;
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
-    const size_t n = (size_t)gh->n_views * gh->nv * gh->nu;
-    const int zw = back_window(gh, sizeof(T) == 8);
+    const int zw = back_window(gh, sizeof(T) == 8, NB);
+    constexpr int kTop = sizeof(T) == 8 ? 128 : 512 / NB;   // largest window instantiated
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
-        prep_sino_3d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (int)pdt, (int)batch, (int)b0, n, ps);
+        dim3 tb(32, 8), tg((gh->nu + 1 + 31) / 32, (gh->nv + 2 + 31) / 32, gh->n_views);
+        prep_diff_3d<T, NB><<<tg, tb, 0, st>>>(p, (int)pdt, (int)batch, (int)b0, gh->nu, gh->nv, ps);
         csm_status r;
-        if (sizeof(T) == 4 && zw == 256) r = launch_back3<T, NB, (sizeof(T) == 4 ? 256 : 128)>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
+        if (zw >= kTop) r = launch_back3<T, NB, kTop>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
+        else if (zw >= 256) r = launch_back3<T, NB, (kTop >= 256 ? 256 : 64)>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
         else if (zw == 128) r = launch_back3<T, NB, 128>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
         else r = launch_back3<T, NB, 64>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
         if (r != CSM_OK) return r;
@@ -885,7 +1218,8 @@ csm_status forward_3d(const csm_geom_s* g, const void* x, void* p, int64_t batch
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     if (flags & CSM_VOXEL_DRIVEN) return CSM_EUNSUPPORTED;
     if (!ws || ws_bytes < workspace_3d(g, 0, batch, dbl)) return CSM_EINVAL;
-    if (g->n_views > 65535 || (g->nv + 31) / 32 > 65535) return CSM_EUNSUPPORTED;
+    if (g->n_views > 65535 || (g->nv + 31) / 32 > 65535 || g->ny > 65535 || (g->nz + 31) / 32 > 65535)
+        return CSM_EUNSUPPORTED;
     switch (chunk3(batch)) {
         case 4: return dbl ? run_fwd3<double, 4>(g, x, p, batch, xdt, pdt, flags, ws, st)
                            : run_fwd3<float, 4>(g, x, p, batch, xdt, pdt, flags, ws, st);
@@ -900,7 +1234,7 @@ csm_status back_3d(const csm_geom_s* g, const void* p, void* x, int64_t batch, c
                    int flags, void* ws, size_t ws_bytes, cudaStream_t st) {
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     if (!ws || ws_bytes < workspace_3d(g, 1, batch, dbl)) return CSM_EINVAL;
-    if ((g->nz + 63) / 64 > 65535) return CSM_EUNSUPPORTED;
+    if ((g->nz + 63) / 64 > 65535 || g->n_views > 65535 || (g->nv + 31) / 32 > 65535) return CSM_EUNSUPPORTED;
     switch (chunk3(batch)) {
         case 4: return dbl ? run_back3<double, 4>(g, p, x, batch, pdt, xdt, flags, ws, st)
                            : run_back3<float, 4>(g, p, x, batch, pdt, xdt, flags, ws, st);
