@@ -909,6 +909,123 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
 // before any table is built.  The window is as tall as a shared-memory budget allows (384
 // rows for one FP32 batch item).
 // ---------------------------------------------------------------------------------------
+// ---------------------------------------------------------------------------------------
+// One cell of the forward projection in the fast form, the lanes taking row planes.  With
+// C_a(r) = sum_iz x(iz) Phi_a(r, iz) for atom a (whole cell or below a crossing line) and
+// plane r, an element column k of the footprint receives on row l
+//     p(k, l) += sigma [T(line k + 1, l) - T(line k, l)],   T_a(l) = C_a(l + 1) - C_a(l),
+// with T = 0 or T of the whole cell for the lines outside the footprint (as in voxel_entries).
+// Plane r has its centre in voxel i_r (height h in [0, 1) above its bottom): every voxel
+// below it has Phi = c A, voxel i_r the linear Phi, and a face the plane meets inside the cell
+// moves K from one side to the other, so
+//     C_a(r) = c A_a X(i_r) + C'_a(r),  C'_a(r) = (g A_a + q M1_a) x(i_r) + K_a (x above - x below)
+// (X: the sum of x below a voxel) and T_a(l) = c A_a [x(i_l) + .. + x(i_{l+1} - 1)] + C'_a(l+1)
+// - C'_a(l).  Each lane computes C' of its plane, takes its neighbour's (plane l + 1) by a
+// shuffle, and adds its row's sums: rows are owned by lanes (no atomics, fixed order).  Rows
+// whose two planes both lie below or both above the grid get T = 0 and are skipped.
+// ---------------------------------------------------------------------------------------
+template <typename T, int NB>
+__device__ __forceinline__ void cell_forward_fast(const Geo& g, const ColumnView<T>& cv, const AtomP<T>* atoms,
+                                                  const AtomP<T>& full, const T* __restrict__ xcol, int lane, int kg,
+                                                  int nk, int L0, int nrow, int rw, T* rows) {
+    const T c = G3<T>::c(g);
+    const int ng = cv.ng, na = ng + 1;
+    // planes that can reach into the grid: around the heights -1 and nz + 1 (m < 1/2)
+    const T tc = cv.dh + cv.dl;
+    const T ra_f = (G3<T>::div(T(-1) - T(0.5) * T(g.nz), tc) * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
+    const T rb_f = (G3<T>::div(T(g.nz + 1) - T(0.5) * T(g.nz), tc) * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
+    const int plast = L0 + nrow;                      // planes L0 .. L0 + nrow bound the window's rows
+    int r_first = L0, r_last = plast;
+    {
+        const T lo = floor(ra_f) - T(1), hi = floor(rb_f) + T(2);
+        if (lo > T(r_first)) r_first = lo > T(plast) ? plast : (int)lo;
+        if (hi < T(r_last)) r_last = hi < T(r_first) ? r_first : (int)hi;
+    }
+    auto xat = [&](int iz, int n) { return (iz >= 0 && iz < g.nz) ? __ldg(xcol + (size_t)iz * NB + n) : T(0); };
+#pragma unroll 1
+    for (int rc = r_first; rc < r_last; rc += 31) {
+        const int r = rc + lane;
+        T cp[kMaxG + 1][NB];
+#pragma unroll
+        for (int j = 0; j <= kMaxG; ++j)
+#pragma unroll
+            for (int n = 0; n < NB; ++n) cp[j][n] = T(0);
+        int izr = 0;
+        if (r <= r_last) {
+            T q, iq;
+            const T H = plane_height(g, r, 0, cv.dh, cv.dl, q, iq);   // height above the grid's bottom
+            izr = (int)floor(H);
+            T h = plane_height(g, r, izr, cv.dh, cv.dl, q, iq);       // the same, relative to voxel izr
+            if (h < T(0)) { izr -= 1; h += T(1); }
+            else if (h >= T(1)) { izr += 1; h -= T(1); }
+            const T m = fabs(q) * cv.margin_c;
+            T x0[NB], dx[NB];
+            const bool kb = h < m, kt = h > T(1) - m;
+#pragma unroll
+            for (int n = 0; n < NB; ++n) {
+                x0[n] = xat(izr, n);
+                dx[n] = kb ? x0[n] - xat(izr - 1, n) : (kt ? xat(izr + 1, n) - x0[n] : T(0));
+            }
+            const T gw = h * c;
+            const T gk = kb ? gw : gw - c;      // height above the face the plane meets
+#pragma unroll
+            for (int j = 0; j <= kMaxG; ++j) {
+                if (j < na) {
+                    const AtomP<T>& P = j == 0 ? full : atoms[j - 1];
+                    const T L = gw * P.A + q * P.M1;
+                    T K = T(0);
+                    if (kb || kt) K = kink_tail<T>(P, gk, q, iq, kt);
+#pragma unroll
+                    for (int n = 0; n < NB; ++n) cp[j][n] = L * x0[n] + K * dx[n];
+                }
+            }
+        }
+        const int izn = __shfl_down_sync(0xffffffffu, izr, 1);
+        T tv[kMaxG + 1][NB];
+#pragma unroll
+        for (int j = 0; j <= kMaxG; ++j) {
+            if (j < na) {
+#pragma unroll
+                for (int n = 0; n < NB; ++n) tv[j][n] = __shfl_down_sync(0xffffffffu, cp[j][n], 1) - cp[j][n];
+            }
+        }
+        const int l = r;
+        if (lane < 31 && l < r_last) {
+            // voxels from i_l up to i_{l+1} - 1 lie between the two planes
+            T sx[NB];
+#pragma unroll
+            for (int n = 0; n < NB; ++n) sx[n] = T(0);
+            const int za = izr < 0 ? 0 : izr, zb = izn > g.nz ? g.nz : izn;
+            for (int iz = za; iz < zb; ++iz) {
+#pragma unroll
+                for (int n = 0; n < NB; ++n) sx[n] += __ldg(xcol + (size_t)iz * NB + n);
+            }
+            T* row = rows + (size_t)(l - L0) * NB;
+            T sf[NB], prev[NB];
+#pragma unroll
+            for (int n = 0; n < NB; ++n) {
+                sf[n] = tv[0][n] + c * full.A * sx[n];
+                prev[n] = cv.sigma > 0 ? T(0) : sf[n];
+            }
+#pragma unroll
+            for (int j = 0; j <= kMaxG; ++j) {
+                if (j <= ng) {
+                    const int k = cv.k_first + j;
+                    const bool inside = k >= kg && k < kg + nk;
+                    const T cA = j < ng ? c * atoms[j < kMaxG ? j : kMaxG - 1].A : T(0);
+#pragma unroll
+                    for (int n = 0; n < NB; ++n) {
+                        const T S = j < ng ? tv[j < kMaxG ? j + 1 : kMaxG][n] + cA * sx[n] : (cv.sigma > 0 ? sf[n] : T(0));
+                        const T wt = cv.sigma > 0 ? S - prev[n] : prev[n] - S;
+                        if (inside) row[(size_t)(k - kg) * rw * NB + n] += wt;
+                        prev[n] = S;
+                    }
+                }
+            }
+        }
+    }
+}
+
 constexpr int FW = 4;                // warps per block
 
 // Sink of the forward projection: W x added to the (column, row) sums of the warp's group.
@@ -932,7 +1049,6 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
                                                      const T* __restrict__ xs1, void* __restrict__ p, int pdt,
                                                      int B, int b_off, T scale, int accumulate) {
     __shared__ AtomP<T> atoms_s[FW][kMaxG + 1];
-    __shared__ T ks_s[FW][32 * kKs];
     extern __shared__ __align__(16) unsigned char fwd_dyn[];   // [FW][KW][rw][NB] sums
     using L = typename LineOf<T>::type;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -944,7 +1060,6 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
     T* rows = reinterpret_cast<T*>(fwd_dyn) + (size_t)wid * KW * rw * NB;   // [(k - kg) * rw + row][NB]
     for (int i = lane; i < KW * rw * NB; i += 32) rows[i] = T(0);
     AtomP<T>* atoms = atoms_s[wid];
-    T* ks = ks_s[wid];
     const int axis = g.axis_sigma[2 * v];
     const int nc = axis == 0 ? g.ny : g.nx;
     const T* __restrict__ xs = axis == 0 ? xs0 : xs1;
@@ -1007,32 +1122,8 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             }
             __syncwarp();
             if (cv.fast) {
-                // 31 voxels per pass; lane 31 finds the face above the last of them.  A face's
-                // correction is needed only when the voxel above or below it is nonzero.
-                for (int zc = izlo; zc <= izhi; zc += 31) {
-                    const int iz = zc + lane;
-                    T xv[NB];
-                    bool own = false;
-#pragma unroll
-                    for (int i = 0; i < NB; ++i) {
-                        xv[i] = (lane < 31 && iz <= izhi) ? __ldg(xcol + (size_t)iz * NB + i) : T(0);
-                        own |= xv[i] != T(0);
-                    }
-                    const bool below = __shfl_up_sync(0xffffffffu, own, 1);
-                    const bool need = own || (lane > 0 && below);
-                    int ra = 0;
-                    const int rb = (need && iz <= izhi + 1) ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
-                    __syncwarp();
-                    const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
-                    if (own) {
-                        RowSink<T, NB> sink{rows, rw, kg, nk, L0, nrow};
-#pragma unroll
-                        for (int i = 0; i < NB; ++i) sink.xv[i] = xv[i];
-                        voxel_entries_fast<T>(g, ix, iy, iz, cv, atoms, atoms[kMaxG], rb, ks + lane * kKs, rt,
-                                              ks + (lane + 1) * kKs, sink);
-                    }
-                    __syncwarp();
-                }
+                cell_forward_fast<T, NB>(g, cv, atoms, atoms[kMaxG], xcol, lane, kg, nk, L0, nrow, rw, rows);
+                __syncwarp();
                 continue;
             }
             for (int zb = izlo; zb <= izhi; zb += 32) {
