@@ -60,6 +60,7 @@ typedef enum { CSM_F32 = 0, CSM_F64 = 1, CSM_BF16 = 2, CSM_F16 = 3 } csm_dtype;
                                      paper's A_3, A_4, Vol_rel                                */
 #define CSM_VOXEL_DRIVEN      4   /* forward only: the voxel-driven scatter variant; not built
                                      (CSM_EUNSUPPORTED): the ray-driven gather is the forward */
+#define CSM_EXPORT_TRANSPOSE  8   /* csm_export_csr: rows are voxels (the CSR of W^T)         */
 
 /* 2D fan-beam geometry.  angles == NULL means phi_v = 2 pi v / n_views. */
 typedef struct {
@@ -162,6 +163,12 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
                      const double* a_den, const void* x, double b_c, const double* b_num,
                      const double* b_den, void* y, int flags, void* cuda_stream);
 
+/* out[i] = num[i] / den[i] for i < n, and 0 where den[i] == 0 (dt = CSM_F32 or CSM_F64; device
+ * arrays, out may alias num).  The data scaling of SART (the measured projections divided by
+ * the row sums of W).  Asynchronous on the stream. */
+csm_status csm_ediv(int64_t n, csm_dtype dt, const void* num, const void* den, void* out,
+                    void* cuda_stream);
+
 /* csm_dot without a workspace argument, for callers that cannot allocate device memory
  * (e.g. everything is owned by a pool allocator, a plug-in given no allocator, or a loop
  * where the device synchronisation cudaMalloc / cudaFree may cause is not acceptable).  The
@@ -192,6 +199,46 @@ csm_status csm_dot_noalloc(const void* a, const void* c, int64_t n, int64_t batc
  * counts, other dtypes), CSM_ECUDA. */
 csm_status csm_fma_rate(csm_dtype dt, int64_t iters, int blocks_per_sm, int launches,
                         double* flops, double* seconds, void* cuda_stream);
+
+/* ---- the system matrix as an explicit sparse matrix -------------------------------------
+ * The paper writes the reconstruction problem with W as a matrix (Introduction, Eq. (ip):
+ * p = W u) and names the algebraic row-action methods (ART, SART) among the reconstruction
+ * methods.  For problems small enough to store W, csm_export_csr writes it in CSR form,
+ * computed on the device from the same closed-form entries as csm_forward / csm_back.
+ *
+ * Rows are detector elements, row index (view nv + l) nu + k, columns voxels (x layout
+ * index); with CSM_EXPORT_TRANSPOSE rows are voxels and columns elements (the CSR of W^T).
+ * Column indices are sorted within each row.  Stored entries are those whose value exceeds
+ * the resolution of the arithmetic: 1e-6 of the voxel's area / volume for CSM_F32 values (the
+ * entries csm_nnz counts), 1e-12 for CSM_F64; values are areas / volumes, or fractions of
+ * the voxel with CSM_RELATIVE_WEIGHTS.  flags: CSM_EXPORT_TRANSPOSE | CSM_RELATIVE_WEIGHTS.
+ *   row_ptr : device array of n_rows + 1 int64 (n_rows = voxels or views x nv x nu), written
+ *   col_idx, val : device arrays of `capacity` entries (int32, val_dt = CSM_F32 or CSM_F64);
+ *             both NULL: only row_ptr and *nnz are computed
+ *   nnz     : host pointer, receives the number of stored entries
+ *   workspace : device scratch of csm_export_workspace_bytes(geom, flags) bytes
+ * Synchronises the stream.  Errors: CSM_EINVAL (NULL pointers, capacity < *nnz (with *nnz
+ * set), workspace too small, another device current), CSM_EUNSUPPORTED (2^31 or more rows or
+ * columns), CSM_ECUDA. */
+csm_status csm_export_workspace_bytes(csm_geom_t geom, int flags, size_t* bytes);
+csm_status csm_export_csr(csm_geom_t geom, int flags, csm_dtype val_dt, int64_t* row_ptr,
+                          int32_t* col_idx, void* val, int64_t capacity, int64_t* nnz,
+                          void* workspace, size_t workspace_bytes, void* cuda_stream);
+
+/* y = alpha A x + beta y for a CSR matrix A with n_rows rows (row_ptr int64, col_idx int32,
+ * val / x / y device arrays of dt = CSM_F32 or CSM_F64), a warp per row summing in a fixed
+ * order (bit-reproducible); beta = 0 does not read y.  With the CSR of W this is the forward
+ * projection, with the CSR of W^T the back projection.  Asynchronous on the stream. */
+csm_status csm_csr_spmv(int64_t n_rows, const int64_t* row_ptr, const int32_t* col_idx,
+                        const void* val, csm_dtype dt, double alpha, const void* x,
+                        double beta, void* y, void* cuda_stream);
+
+/* Divides each row of a CSR matrix (values val, dt = CSM_F32 or CSM_F64) by its sum, in
+ * place; rows summing to 0 are left unchanged.  row_sums: NULL or a device array of n_rows
+ * values of dt receiving the sums.  The row and column normalisations of SART (W divided by
+ * its row sums, W^T by the column sums of W).  Asynchronous on the stream. */
+csm_status csm_csr_normalize_rows(int64_t n_rows, const int64_t* row_ptr, void* val,
+                                  csm_dtype dt, void* row_sums, void* cuda_stream);
 
 /* Waits for the stream and reports an asynchronous kernel failure as CSM_ECUDA. */
 csm_status csm_sync_status(void* cuda_stream);

@@ -23,6 +23,7 @@ CSM_F32, CSM_F64, CSM_BF16, CSM_F16 = range(4)
 CSM_ACCUMULATE = 1
 CSM_RELATIVE_WEIGHTS = 2
 CSM_VOXEL_DRIVEN = 4
+CSM_EXPORT_TRANSPOSE = 8
 
 
 class csm_geom2d_desc(C.Structure):
@@ -72,6 +73,18 @@ lib.csm_dot_noalloc.restype = _st
 lib.csm_fma_rate.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.c_void_p]
 lib.csm_fma_rate.restype = _st
+lib.csm_export_workspace_bytes.argtypes = [csm_geom_t, C.c_int, C.POINTER(C.c_size_t)]
+lib.csm_export_workspace_bytes.restype = _st
+lib.csm_export_csr.argtypes = [csm_geom_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                               C.POINTER(C.c_int64), C.c_void_p, C.c_size_t, C.c_void_p]
+lib.csm_export_csr.restype = _st
+lib.csm_csr_spmv.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.c_void_p,
+                             C.c_double, C.c_void_p, C.c_void_p]
+lib.csm_csr_spmv.restype = _st
+lib.csm_csr_normalize_rows.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+lib.csm_csr_normalize_rows.restype = _st
+lib.csm_ediv.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+lib.csm_ediv.restype = _st
 lib.csm_sync_status.argtypes = [C.c_void_p]
 lib.csm_sync_status.restype = _st
 lib.csm_status_string.argtypes = [_st]
@@ -83,7 +96,8 @@ EXPORTED = [
     "csm_geom_create_2d", "csm_geom_create_3d", "csm_geom_free", "csm_workspace_bytes",
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
     "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
-    "csm_fma_rate",
+    "csm_fma_rate", "csm_export_workspace_bytes", "csm_export_csr", "csm_csr_spmv", "csm_csr_normalize_rows",
+    "csm_ediv",
 ]
 CSM_DOT_NOALLOC_MAX_BATCH = 64
 
@@ -167,3 +181,31 @@ def csm_fma_rate(dt, iters, blocks_per_sm, launches, stream) -> tuple[float, flo
     f, t = C.c_double(), C.c_double()
     check(lib.csm_fma_rate(dt, iters, blocks_per_sm, launches, C.byref(f), C.byref(t), stream), "csm_fma_rate")
     return f.value, t.value
+
+
+def csm_export_workspace_bytes(h, flags) -> int:
+    n = C.c_size_t()
+    check(lib.csm_export_workspace_bytes(h, flags, C.byref(n)), "csm_export_workspace_bytes")
+    return n.value
+
+
+def csm_export_csr(h, flags, val_dt, row_ptr, col_idx, val, capacity, ws_ptr, ws_bytes, stream) -> int:
+    """Writes the CSR arrays (col_idx / val may be None for the count only); returns nnz."""
+    n = C.c_int64()
+    st = lib.csm_export_csr(h, flags, val_dt, row_ptr, col_idx, val, capacity, C.byref(n), ws_ptr, ws_bytes, stream)
+    if st == CSM_EINVAL and col_idx and capacity < n.value:
+        raise CsmError(st, "csm_export_csr (capacity %d < nnz %d)" % (capacity, n.value))
+    check(st, "csm_export_csr")
+    return n.value
+
+
+def csm_csr_spmv(n_rows, row_ptr, col_idx, val, dt, alpha, x, beta, y, stream) -> None:
+    check(lib.csm_csr_spmv(n_rows, row_ptr, col_idx, val, dt, alpha, x, beta, y, stream), "csm_csr_spmv")
+
+
+def csm_csr_normalize_rows(n_rows, row_ptr, val, dt, row_sums, stream) -> None:
+    check(lib.csm_csr_normalize_rows(n_rows, row_ptr, val, dt, row_sums, stream), "csm_csr_normalize_rows")
+
+
+def csm_ediv(n, dt, num, den, out, stream) -> None:
+    check(lib.csm_ediv(n, dt, num, den, out, stream), "csm_ediv")

@@ -260,6 +260,25 @@ csm_status back_2d(const csm_geom_s* g, const void* p, void* x, int64_t batch, c
 size_t workspace_2d(const csm_geom_s* g, int op, int64_t batch, bool dbl);
 csm_status nnz_2d(const csm_geom_s* g, int64_t* out, cudaStream_t st);
 
+// Sparse export (sparse.cu drives these passes over every entry with |w| > thr, scaled by
+// `scale`).  Rows of W^T are voxels, rows of W detector elements (v nv + l) nu + k.
+//   mode 0: rows of W^T, counts[voxel] = number of entries     (no atomics)
+//   mode 1: rows of W^T, fill from row_ptr in (view, row, column) order (sorted columns)
+//   mode 2: rows of W,   counts[element] += 1                   (atomics)
+//   mode 3: rows of W,   fill at row_ptr[element] + cursor[element]++ (atomics; rows sorted later)
+struct ExportArgs {
+    int mode;
+    double thr, scale;
+    unsigned long long* counts;
+    const long long* row_ptr;
+    int* cursor;
+    int* col;
+    void* val;
+    int dbl;   // values (and arithmetic) in FP64
+};
+csm_status export_2d(const csm_geom_s* g, const ExportArgs& a, cudaStream_t st);
+csm_status export_3d(const csm_geom_s* g, const ExportArgs& a, cudaStream_t st);
+
 csm_status forward_3d(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt,
                       csm_dtype pdt, int flags, void* ws, size_t ws_bytes, cudaStream_t st);
 csm_status back_3d(const csm_geom_s* g, const void* p, void* x, int64_t batch, csm_dtype pdt,

@@ -8,7 +8,7 @@ namespace csm {
 
 constexpr int kPeakChains = 8;     // independent accumulators per thread (hide FMA latency)
 constexpr int kPeakThreads = 256;
-static __device__ double g_peak_sink;   // written only by a result the chains cannot reach
+__device__ double g_peak_sink;   // written only by a result the chains cannot reach
 
 // Every thread runs kPeakChains independent chains a <- a * m + c for `iters` rounds (2 flops
 // per FMA).  m and c come from the host, so the compiler cannot fold the chains; the result

@@ -387,6 +387,68 @@ __global__ void __launch_bounds__(256) nnz2d_kernel(Geo g, unsigned long long* c
     if ((threadIdx.x + 16 * threadIdx.y) % 32 == 0 && cnt) atomicAdd(counter, cnt);
 }
 
+// Sparse export: thread per pixel, its entries in view then element order (the back
+// projection's cell atoms), written as rows of W^T (pixels) or of W (elements) as described by
+// ExportArgs in csm_internal.cuh.
+template <typename T>
+__global__ void __launch_bounds__(256) export2d_kernel(Geo g, ExportArgs ea) {
+    const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const long long pix = (long long)iy * g.nx + ix;
+    const T thr = (T)ea.thr, scale = (T)ea.scale;
+    const T X0 = GeoT<T>::x0(g) + ix * GeoT<T>::a(g), X1 = X0 + GeoT<T>::a(g);
+    const T Y0 = GeoT<T>::y0(g) + iy * GeoT<T>::b(g), Y1 = Y0 + GeoT<T>::b(g);
+    using L = typename LineOf<T>::type;
+    long long n = 0;
+    for (int v = 0; v < g.n_views; ++v) {
+        int k0, k1;
+        if (!pixel_elements<T>(g, v, X0, X1, Y0, Y1, k0, k1)) continue;
+        const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+        const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
+        L l;
+        l.load(g, v, k0, w);
+        T y0, y1;
+        l.offsets(c, y0, y1);
+        T prev = cell_atom(y0, y1, inv_of<T>(g, v, k0));
+        for (int k = k0; k <= k1; ++k) {
+            l.load(g, v, k + 1, w);
+            l.offsets(c, y0, y1);
+            const T cur = cell_atom(y0, y1, inv_of<T>(g, v, k + 1));
+            const T wt = sigma > 0 ? cur - prev : prev - cur;
+            prev = cur;
+            if (!(fabs(wt) > thr)) continue;
+            const long long row_e = (long long)v * g.nu + k;
+            switch (ea.mode) {
+                case 0: ++n; break;
+                case 1: {
+                    const long long slot = ea.row_ptr[pix] + n++;
+                    ea.col[slot] = (int)row_e;
+                    if (ea.dbl) ((double*)ea.val)[slot] = (double)(wt * scale);
+                    else ((float*)ea.val)[slot] = (float)(wt * scale);
+                    break;
+                }
+                case 2: atomicAdd(ea.counts + row_e, 1ull); break;
+                default: {
+                    const long long slot = ea.row_ptr[row_e] + atomicAdd(ea.cursor + row_e, 1);
+                    ea.col[slot] = (int)pix;
+                    if (ea.dbl) ((double*)ea.val)[slot] = (double)(wt * scale);
+                    else ((float*)ea.val)[slot] = (float)(wt * scale);
+                    break;
+                }
+            }
+        }
+    }
+    if (ea.mode == 0) ea.counts[pix] = (unsigned long long)n;
+}
+
+csm_status export_2d(const csm_geom_s* gh, const ExportArgs& a, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16);
+    if (a.dbl) export2d_kernel<double><<<bg, bb, 0, st>>>(g, a);
+    else export2d_kernel<float><<<bg, bb, 0, st>>>(g, a);
+    return check_launch();
+}
+
 // ---------------------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------------------

@@ -1215,6 +1215,115 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
 }
 
 // ---------------------------------------------------------------------------------------
+// Sparse export: the same per-voxel entries (column-warps, 64-voxel windows as the count),
+// written as rows of W^T (voxels; per-voxel counts and write positions kept in shared memory,
+// so the entries of a row come in view, row, column order) or of W (elements; atomics).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct ExportSink {
+    ExportArgs a;
+    T thr, scale;
+    long long vox;     // this voxel's index (column of W)
+    int base;          // row index of this view's first element
+    int nu;
+    int n;             // entries so far (mode 0) / write position (mode 1)
+    __device__ __forceinline__ void add(int k, int l, T wt) {
+        if (!(fabs(wt) > thr)) return;
+        const long long row_e = (long long)base + (long long)l * nu + k;
+        switch (a.mode) {
+            case 0: ++n; break;
+            case 1: {
+                const long long slot = a.row_ptr[vox] + n++;
+                a.col[slot] = (int)row_e;
+                if (a.dbl) ((double*)a.val)[slot] = (double)(wt * scale);
+                else ((float*)a.val)[slot] = (float)(wt * scale);
+                break;
+            }
+            case 2: atomicAdd(a.counts + row_e, 1ull); break;
+            default: {
+                const long long slot = a.row_ptr[row_e] + atomicAdd(a.cursor + row_e, 1);
+                a.col[slot] = (int)vox;
+                if (a.dbl) ((double*)a.val)[slot] = (double)(wt * scale);
+                else ((float*)a.val)[slot] = (float)(wt * scale);
+                break;
+            }
+        }
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(32 * BW) export3d_kernel(Geo g, ExportArgs ea) {
+    __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
+    __shared__ T ks_s[BW][32 * kKs];
+    __shared__ int pos_s[BW][ZWN];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int col = blockIdx.x * BW + wid;
+    if (col >= g.nx * g.ny) return;
+    const int ix = col % g.nx, iy = col / g.nx;
+    const int zb = blockIdx.y * ZWN, ze = min(zb + ZWN, g.nz);
+    AtomP<T>* atoms = atoms_s[wid];
+    T* ks = ks_s[wid];
+    int* pos = pos_s[wid];
+    for (int i = lane; i < ZWN; i += 32) pos[i] = 0;
+    ExportSink<T> sink;
+    sink.a = ea;
+    sink.thr = (T)ea.thr;
+    sink.scale = (T)ea.scale;
+    sink.nu = g.nu;
+    for (int v = 0; v < g.n_views; ++v) {
+        ColumnView<T> cv;
+        column_view<T>(g, v, ix, iy, lane, cv);
+        if (!cv.ok) continue;
+        int z0, z1;
+        cone_z_range<T>(g, cv.tmin_w, cv.tmax_w, z0, z1);
+        z0 = max(z0, zb);
+        z1 = min(z1, ze - 1);
+        if (z0 > z1) continue;
+        __syncwarp();
+        column_atoms<T>(g, v, ix, iy, cv, lane, atoms);
+        __syncwarp();
+        sink.base = v * g.nv * g.nu;
+        if (cv.fast) {
+            for (int zc = z0; zc <= z1; zc += 31) {
+                const int iz = zc + lane;
+                int ra = 0;
+                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                __syncwarp();
+                const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
+                if (lane < 31 && iz <= z1) {
+                    sink.vox = ((long long)iz * g.ny + iy) * g.nx + ix;
+                    sink.n = pos[iz - zb];
+                    voxel_entries_fast<T>(g, ix, iy, iz, cv, atoms, atoms[kMaxG], rb, ks + lane * kKs, rt,
+                                          ks + (lane + 1) * kKs, sink);
+                    pos[iz - zb] = sink.n;
+                }
+                __syncwarp();
+            }
+        } else {
+            for (int iz = z0 + lane; iz <= z1; iz += 32) {
+                sink.vox = ((long long)iz * g.ny + iy) * g.nx + ix;
+                sink.n = pos[iz - zb];
+                voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
+                pos[iz - zb] = sink.n;
+            }
+        }
+    }
+    __syncwarp();
+    if (ea.mode == 0)
+        for (int iz = zb + lane; iz < ze; iz += 32)
+            ea.counts[((long long)iz * g.ny + iy) * g.nx + ix] = (unsigned long long)pos[iz - zb];
+}
+
+csm_status export_3d(const csm_geom_s* gh, const ExportArgs& a, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    const size_t ncol = (size_t)gh->nx * gh->ny;
+    dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZWN - 1) / ZWN);
+    if (a.dbl) export3d_kernel<double><<<bg, bb, 0, st>>>(g, a);
+    else export3d_kernel<float><<<bg, bb, 0, st>>>(g, a);
+    return check_launch();
+}
+
+// ---------------------------------------------------------------------------------------
 // Host dispatch
 // ---------------------------------------------------------------------------------------
 // Rows per forward warp: all of them when the block's row sums fit the shared-memory budget,

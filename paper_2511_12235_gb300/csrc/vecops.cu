@@ -101,6 +101,20 @@ __global__ void axpby_kernel(int64_t n, int64_t batch, int dt, double ac, const 
     }
 }
 
+// out[i] = num[i] / den[i], 0 where den[i] == 0
+__global__ void ediv_kernel(int64_t n, int dt, const void* __restrict__ num, const void* __restrict__ den,
+                            void* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (dt == CSM_F64) {
+            const double d = ((const double*)den)[i];
+            ((double*)out)[i] = d != 0.0 ? ((const double*)num)[i] / d : 0.0;
+        } else {
+            const float d = ((const float*)den)[i];
+            ((float*)out)[i] = d != 0.0f ? ((const float*)num)[i] / d : 0.0f;
+        }
+    }
+}
+
 size_t dot_workspace_bytes(int64_t batch) { return (size_t)batch * kDotBlocks * sizeof(double); }
 
 csm_status dot_launch(const void* a, const void* b, int64_t n, int64_t batch, csm_dtype dt, double* out,
@@ -218,6 +232,16 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
     dim3 grid((unsigned)blocks, (unsigned)batch);
     axpby_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, batch, (int)dt, a_c, a_num, a_den, x, b_c, b_num, b_den,
                                                         y, flags);
+    return check_launch();
+}
+
+csm_status csm_ediv(int64_t n, csm_dtype dt, const void* num, const void* den, void* out, void* stream) {
+    if (n < 0 || (n > 0 && (!num || !den || !out))) return CSM_EINVAL;
+    if (dt != CSM_F32 && dt != CSM_F64) return CSM_EINVAL;
+    if (n == 0) return CSM_OK;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 1216) blocks = 1216;
+    ediv_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, (int)dt, num, den, out);
     return check_launch();
 }
 
