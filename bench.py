@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(WORKLOADS) + ["serving"])
-    ap.add_argument("--requests", type=int, default=60, help="serving: number of requests")
+    ap.add_argument("--requests", type=int, default=200, help="serving: number of requests")
     ap.add_argument("--load", type=float, default=0.7, help="serving: arrival rate / measured capacity")
     ap.add_argument("--sweep", type=str, default="",
                     help="serving: further loads to run after --load, comma separated (e.g. 0.5,0.9)")
@@ -549,9 +549,10 @@ def run_ours(args, rank, world, local):
 
 
 def run_serving(args, rank, world, local):
-    """Serving mix: Poisson arrivals of reconstruction requests (60% 2D, 40% 3D, 20 NAG
-    iterations each), served by the continuous-batching server against the same requests run
-    one at a time with plain calls.  Rank 0 only (one server per GPU)."""
+    """Serving mix: Poisson arrivals of reconstruction requests (60% 2D, 40% 3D on fixed scanner
+    protocols, 20 NAG iterations each), served by the continuous-batching server, against
+    the same requests run for real one at a time with plain calls.  Rank 0 only (one server
+    per GPU)."""
     import numpy as np
     import torch
     if rank != 0:
@@ -560,10 +561,9 @@ def run_serving(args, rank, world, local):
     dev = torch.device("cuda", local)
     import synth
     import paper_2511_12235_gb300 as csm
-    from paper_2511_12235_gb300.serve import (ReconServer, Request, fifo_latencies, latency_stats,
-                                              solve_alone)
+    from paper_2511_12235_gb300.serve import ReconServer, Request, latency_stats, serve_unbatched
     specs = synth.serving_requests(args.requests, seed=0, rate_per_s=1.0)
-    reqs = []
+    base = []
     for sp in specs:      # measured data: projections of a seeded phantom with Poisson noise
         g = sp["geom"]
         P = csm.Projector(g, device=dev)
@@ -574,72 +574,75 @@ def run_serving(args, rank, world, local):
         p = P.forward(x).double().cpu().numpy()
         P.close()
         pn, _ = synth.poisson_sinogram(p, seed=sp["seed"])
-        reqs.append(Request(id=sp["id"], geom=g, sino=pn.astype(np.float32), iters=20, power_iters=20,
-                            seed=sp["seed"]))
+        base.append(dict(id=sp["id"], geom=g, sino=pn.astype(np.float32), iters=20, power_iters=20, seed=sp["seed"]))
     torch.cuda.synchronize()
-    # unbatched plain calls, one request at a time: the service time of each request
-    solve_alone(reqs[0], device=dev)          # warm-up
-    service = []
-    for r in reqs:
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        solve_alone(r, device=dev)
-        torch.cuda.synchronize()
-        service.append(time.perf_counter() - t0)
-    n = len(reqs)
-    # throughput: every request waiting at t = 0; the unbatched server takes them one by one
-    srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
+    n = len(base)
+    fresh = lambda: [Request(**b) for b in base]
+    kinds = np.array([b["geom"]["dim"] for b in base])
+    # unbatched plain calls, one at a time, all waiting: the service time of every request
+    serve_unbatched(fresh()[:1], device=dev, realtime=False)          # warm-up
+    alone = serve_unbatched(fresh(), device=dev, realtime=False)
+    service = np.array([r.t_done - r.t_admit for r in alone])
+    unb_makespan = max(r.t_done for r in alone)
+    # throughput: every request waiting at t = 0
+    srv = ReconServer(device=dev, budget_bytes=120 << 30, use_graphs=True)
     t0 = time.perf_counter()
-    srv.serve(reqs, realtime=False)
+    sat = srv.serve(fresh(), realtime=False)
     makespan = time.perf_counter() - t0
+    stats_sat = dict(joined=srv.joined, max_occupancy=srv.max_occupancy, batch_hits=srv.batch_hits)
     srv.close()
-    results_sat = [r.result for r in reqs]
-    # latency: Poisson arrivals at `load` times the unbatched capacity
+    worst = 0.0
+    for r, a in zip(sorted(sat, key=lambda r: r.id), sorted(alone, key=lambda r: r.id)):
+        worst = max(worst, float(np.linalg.norm(r.result - a.result) / max(np.linalg.norm(a.result), 1e-30)))
+    # latency: Poisson arrivals at `load` times the unbatched capacity, both servers run for real
     cap = 1.0 / float(np.mean(service))
-    kinds = np.array([r.geom["dim"] for r in reqs])
 
     def latency_run(load, seed):
         rate = load * cap
         rng = np.random.default_rng(seed)
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
-        for r, a in zip(reqs, arrivals):
-            r.arrival = float(a)
-            r.result = None
-        base_lat = np.array(fifo_latencies(arrivals, service))
-        srv = ReconServer(device=dev, budget_bytes=120 << 30, max_active=16, use_graphs=True)
+        reqs = fresh()
+        for r, t in zip(reqs, arrivals):
+            r.arrival = float(t)
+        srv = ReconServer(device=dev, budget_bytes=120 << 30, use_graphs=True)
         done = srv.serve(reqs, realtime=True)
+        st_run = dict(joined=srv.joined, max_occupancy=srv.max_occupancy)
         srv.close()
-        lat = np.array([r.latency for r in done])
+        lat = np.array([r.latency for r in sorted(done, key=lambda r: r.id)])
+        ub = fresh()
+        for r, t in zip(ub, arrivals):
+            r.arrival = float(t)
+        serve_unbatched(ub, device=dev, realtime=True)
+        base_lat = np.array([r.latency for r in sorted(ub, key=lambda r: r.id)])
         st, bst = latency_stats(lat), latency_stats(base_lat)
-        med = lambda a, k: float(np.median(a[kinds == k])) if (kinds == k).any() else None
-        return srv, rate, {
-            "load_vs_capacity": load, "arrival_rate_per_s": rate,
-            "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
-            "p50_2d_s": med(lat, 2), "p50_3d_s": med(lat, 3),
-            "unbatched": {"p50_s": bst["p50_s"], "p99_s": bst["p99_s"], "mean_s": bst["mean_s"],
-                          "p50_2d_s": med(base_lat, 2), "p50_3d_s": med(base_lat, 3)}}
+        med = lambda a_, k: float(np.median(a_[kinds == k])) if (kinds == k).any() else None
+        return rate, dict({"load_vs_capacity": load, "arrival_rate_per_s": rate,
+                           "p50_s": st["p50_s"], "p99_s": st["p99_s"], "mean_s": st["mean_s"],
+                           "p50_2d_s": med(lat, 2), "p50_3d_s": med(lat, 3),
+                           "unbatched": {"p50_s": bst["p50_s"], "p99_s": bst["p99_s"], "mean_s": bst["mean_s"],
+                                         "p50_2d_s": med(base_lat, 2), "p50_3d_s": med(base_lat, 3)}}, **st_run)
 
-    srv, rate, main_run = latency_run(args.load, 1)
-    same = all(np.array_equal(a, r.result) or np.allclose(a, r.result, rtol=1e-4, atol=1e-6)
-               for a, r in zip(results_sat, reqs))
-    sweep = [latency_run(float(ld), 2 + i)[2] for i, ld in enumerate(x for x in args.sweep.split(",") if x)]
+    rate, main_run = latency_run(args.load, 1)
+    sweep = [latency_run(float(ld), 2 + i)[1] for i, ld in enumerate(x for x in args.sweep.split(",") if x)]
     line = {
         "metric": METRIC, "value": n / makespan, "unit": "requests/s", "n_gpus": 1,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serving", "requests": n, "share_2d": float((kinds == 2).mean()),
-                   "nag_iterations": 20, "power_iterations": 20, "budget_gb": 120, "max_active": 16,
-                   "priority_levels": len(srv.levels), "class_caps": list(srv.caps.values()), "aging": srv.aging,
-                   "arrival_rate_per_s": rate, "load_vs_capacity": args.load},
-        "throughput": {"served_requests_per_s": n / makespan, "unbatched_requests_per_s": n / float(np.sum(service)),
-                       "served_makespan_s": makespan, "unbatched_makespan_s": float(np.sum(service)),
-                       "note": "all requests waiting at t = 0"},
+                   "protocols_2d": [list(p) for p in synth.SERVING_PROTOCOLS_2D],
+                   "protocols_3d": [list(p) for p in synth.SERVING_PROTOCOLS_3D],
+                   "nag_iterations": 20, "power_iterations": 20, "budget_gb": 120,
+                   "slots_per_batch": {"2d": 8, "3d": 4}, "arrival_rate_per_s": rate, "load_vs_capacity": args.load},
+        "throughput": {"served_requests_per_s": n / makespan, "unbatched_requests_per_s": n / unb_makespan,
+                       "served_makespan_s": makespan, "unbatched_makespan_s": unb_makespan,
+                       "note": "all requests waiting at t = 0", **stats_sat},
         "p50_s": main_run["p50_s"], "p99_s": main_run["p99_s"], "mean_s": main_run["mean_s"],
         "p50_2d_s": main_run["p50_2d_s"], "p50_3d_s": main_run["p50_3d_s"],
         "unbatched": dict(main_run["unbatched"], mean_service_s=float(np.mean(service)),
-                          note="same requests and arrivals, one at a time with plain csm_forward/csm_back calls "
-                               "(FIFO queue over the measured service times)"),
+                          note="the same requests and arrivals served for real one at a time with plain "
+                               "csm_forward/csm_back calls (FIFO)"),
+        "joined_running_batches": main_run["joined"], "max_occupancy": main_run["max_occupancy"],
         "load_sweep": sweep,
-        "results_equal_across_runs": bool(same),
+        "served_vs_alone_max_rel_l2": worst,
         "service_s": [round(float(x), 4) for x in service],
     }
     print(json.dumps(line), flush=True)

@@ -163,6 +163,16 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
                      const double* a_den, const void* x, double b_c, const double* b_num,
                      const double* b_den, void* y, int flags, void* cuda_stream);
 
+/* The momentum of Nesterov's method (FISTA form, t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2,
+ * theta_k = (t_k - 1) / t_{k+1}) for a batch whose items are at different iterations, as in a
+ * reconstruction server that lets new requests join a running batch: item b reads
+ * theta = theta_table[k[b]] (0 for k[b] outside 0 .. n_table - 1), writes one_plus_theta[b] =
+ * 1 + theta and theta[b] = theta, and increments k[b].  All device arrays (k: int32, the rest
+ * float64); theta_table may be NULL when n_table is 0.  Asynchronous on the stream, so an
+ * iteration can be captured in a CUDA graph and replayed while items come and go. */
+csm_status csm_fista_coeffs(int64_t batch, const double* theta_table, int n_table, int32_t* k,
+                            double* one_plus_theta, double* theta, void* cuda_stream);
+
 /* out[i] = num[i] / den[i] for i < n, and 0 where den[i] == 0 (dt = CSM_F32 or CSM_F64; device
  * arrays, out may alias num).  The data scaling of SART (the measured projections divided by
  * the row sums of W).  Asynchronous on the stream. */

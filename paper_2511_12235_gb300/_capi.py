@@ -83,6 +83,8 @@ lib.csm_csr_spmv.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_
 lib.csm_csr_spmv.restype = _st
 lib.csm_csr_normalize_rows.argtypes = [C.c_int64, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
 lib.csm_csr_normalize_rows.restype = _st
+lib.csm_fista_coeffs.argtypes = [C.c_int64, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+lib.csm_fista_coeffs.restype = _st
 lib.csm_ediv.argtypes = [C.c_int64, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
 lib.csm_ediv.restype = _st
 lib.csm_sync_status.argtypes = [C.c_void_p]
@@ -97,7 +99,7 @@ EXPORTED = [
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
     "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
     "csm_fma_rate", "csm_export_workspace_bytes", "csm_export_csr", "csm_csr_spmv", "csm_csr_normalize_rows",
-    "csm_ediv",
+    "csm_ediv", "csm_fista_coeffs",
 ]
 CSM_DOT_NOALLOC_MAX_BATCH = 64
 
@@ -209,3 +211,7 @@ def csm_csr_normalize_rows(n_rows, row_ptr, val, dt, row_sums, stream) -> None:
 
 def csm_ediv(n, dt, num, den, out, stream) -> None:
     check(lib.csm_ediv(n, dt, num, den, out, stream), "csm_ediv")
+
+
+def csm_fista_coeffs(batch, table, n_table, k, one_plus, theta, stream) -> None:
+    check(lib.csm_fista_coeffs(batch, table, n_table, k, one_plus, theta, stream), "csm_fista_coeffs")

@@ -115,6 +115,19 @@ __global__ void ediv_kernel(int64_t n, int dt, const void* __restrict__ num, con
     }
 }
 
+// Per-slot FISTA momentum for batches whose items are at different iterations: item b takes
+// theta = table[k[b]] (0 beyond the table), writes 1 + theta and theta, and counts k[b] up.
+__global__ void fista_coeffs_kernel(int64_t batch, const double* __restrict__ table, int n_table, int* __restrict__ k,
+                                    double* __restrict__ one_plus, double* __restrict__ theta) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= batch) return;
+    const int kk = k[b];
+    const double th = (kk >= 0 && kk < n_table) ? table[kk] : 0.0;
+    one_plus[b] = 1.0 + th;
+    theta[b] = th;
+    k[b] = kk + 1;
+}
+
 size_t dot_workspace_bytes(int64_t batch) { return (size_t)batch * kDotBlocks * sizeof(double); }
 
 csm_status dot_launch(const void* a, const void* b, int64_t n, int64_t batch, csm_dtype dt, double* out,
@@ -232,6 +245,16 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
     dim3 grid((unsigned)blocks, (unsigned)batch);
     axpby_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, batch, (int)dt, a_c, a_num, a_den, x, b_c, b_num, b_den,
                                                         y, flags);
+    return check_launch();
+}
+
+csm_status csm_fista_coeffs(int64_t batch, const double* theta_table, int n_table, int32_t* k, double* one_plus_theta,
+                            double* theta, void* stream) {
+    if (batch < 0 || n_table < 0 || (batch > 0 && (!k || !one_plus_theta || !theta || (n_table > 0 && !theta_table))))
+        return CSM_EINVAL;
+    if (batch == 0) return CSM_OK;
+    fista_coeffs_kernel<<<(unsigned)((batch + 127) / 128), 128, 0, (cudaStream_t)stream>>>(batch, theta_table, n_table,
+                                                                                          k, one_plus_theta, theta);
     return check_launch();
 }
 

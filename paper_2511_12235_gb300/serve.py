@@ -2,42 +2,37 @@
 
 Each request carries a geometry (2D fan or 3D cone beam), measured projections and a
 number of NAG iterations on the Tikhonov objective (Section "Numerical Experiments",
-Eq. (exp_tikh)).  The server
+Eq. (exp_tikh)).  Requests of one shape bucket -- geometry, iterations, power iterations,
+lambda -- share W, its norm and therefore every projector call, so the server batches them:
 
-* admits requests in arrival order while their device-memory footprint fits a budget
-  (120 GB by default) and a slot of their cost class is free; requests that arrive while
-  others run are admitted as soon as memory and slots free up (a request waiting for a slot
-  of its class does not hold back cheaper ones; one waiting for memory holds back all later
-  ones, so that none starves);
-* runs every admitted request on its own CUDA stream, so the projections of different
-  requests overlap on the GPU; the stream's priority follows the request's estimated cost
-  (cheapest requests highest), so the block scheduler starts the blocks of short requests
-  before the remaining blocks of long ones: a small request does not wait for a large one to
-  drain, which is what a FIFO of whole requests would make it do.  The costlier a class, the
-  fewer of its requests run at once (16, 4, 2, 1 for the four classes by default): one large
-  3D solve already fills the GPU, and large requests sharing it would all finish late.  A
-  request that has already waited longer than its own estimated service time (its cost
-  times the smallest time per cost seen on completed requests) gets a stream one level
-  higher, so that the requests that waited longest are not also the slowest to run;
-* estimates ||W|| by power iteration on the device (the scalar never leaves the GPU) once
-  per geometry: the start vector is seeded by the geometry, so the estimate is a function of
-  the geometry alone and later requests of the same geometry reuse it (after an event on the
-  stream that computed it); then captures the request's NAG iterations once into a CUDA
-  graph and replays it: the whole solve is a single launch.  A finished solve (projector,
-  solver state, graph) is kept per shape bucket -- geometry, iterations, lambda -- and a
-  later request of the same bucket loads its projections into it, resets the iterate and
-  replays the graph, with no new allocation or capture; idle solves count against the memory
-  budget and are released, oldest first, when an admission needs the memory;
-* polls completion events and returns results with their latency.  A request that cannot
-  run (its geometry is refused, its projections have the wrong size, it needs more memory
-  than the whole budget, or its set-up fails with an out-of-memory error) is returned with
-  `error` set and no result; the others are served as usual.
+* A *slot batch* per bucket holds the NAG state of up to C requests (``NAGSlots``) on its
+  own CUDA stream.  One iteration of all its occupied slots is captured once per occupancy
+  n into a CUDA graph and replayed; each slot runs its own momentum sequence (its iteration
+  counter lives on the device), so requests join a running batch at any iteration boundary
+  (continuous batching, as in LLM serving) and leave when their iterations are done: the
+  host queues the copy of their result and moves the last occupied slot into the freed one.
+  Every projector call of a replay serves all the batch's requests at once (the kernels
+  share the geometry of an entry among the batch items).
+* Requests are admitted in arrival order: into a free slot of a batch of their bucket, else
+  into a new batch while its memory (C request footprints) fits the budget (120 GB by
+  default) and a batch slot of the request's cost class is free.  A request waiting for
+  memory holds back all later ones (none starves); one whose class is full does not hold
+  back cheaper ones.  Batch streams are prioritised by cost class (cheapest highest), so a
+  small request's blocks start before the remaining blocks of a large one, and the costlier
+  a class the fewer of its batches run at once (16, 4, 2, 1 for four classes).
+* ||W|| comes from a power iteration on the device, once per geometry (start vector seeded
+  by the geometry); a batch that empties stays idle with its graphs for later requests of
+  its bucket and is released, oldest first, when memory is needed.
+* The host keeps at most two iterations of a batch in flight, so that admissions and
+  read-outs are not queued behind many iterations; it polls events and returns results with
+  their latency.  A request that cannot run (refused geometry, projections of the wrong
+  size, more memory than the whole budget, a failed set-up) comes back with `error` set.
 
-All device work is in the library's kernels; the server only orders it.  Results do not
-depend on which other requests run at the same time beyond rounding: every kernel sees only
-its own request's data, the 2D kernels and all reductions have a fixed order (bit-identical
-results), and the 3D forward adds the entries of one detector row through shared-memory
-atomics of one warp, whose order can change the last bits of an FP32 sum.
+Every device step is a library kernel (projectors, csm_dot / csm_axpby / csm_fista_coeffs).
+A request's result does not depend on the other requests of its batch beyond rounding: each
+batch item's arithmetic is its own (the 2D kernels and the reductions in a fixed order,
+bit-identical; the 3D kernels per item in a fixed order, equal to rounding across batch
+sizes).
 """
 from __future__ import annotations
 
@@ -49,8 +44,8 @@ import torch
 
 from ._capi import CsmError
 from .projector import Projector
-from .sched import admit_order, aged_level, geometry_key, geometry_seed
-from .solvers import NAG, power_norm2_device
+from .sched import admit_order, geometry_key, geometry_seed
+from .solvers import NAG, NAGSlots, power_norm2_device
 
 
 @dataclasses.dataclass
@@ -91,53 +86,54 @@ def priority_range():
 
 
 def footprint_bytes(geom: dict, elem: int = 4) -> int:
-    """Device memory a request holds: NAG state u, y, g (3 volumes), residual and data
+    """Device memory one request holds: NAG state u, y, g (3 volumes), residual and data
     (2 sinograms), power-iteration vectors (2 volumes, 1 sinogram), the projector's
-    workspaces (2 volumes, 1 sinogram) and its geometry table."""
+    workspaces (2 volumes, 1 sinogram; the back projection's differenced sinogram counts
+    as four) and its geometry table."""
     nvox = geom["nx"] * geom["ny"] * geom["nz"]
     nsino = geom["n_views"] * geom.get("nv", 1) * geom["nu"]
     table = geom["n_views"] * (geom["nu"] + 1) * 48 + geom["n_views"] * (geom.get("nv", 1) + 1) * 48
-    return elem * (7 * nvox + 4 * nsino) + table + (1 << 20)
+    return elem * (7 * nvox + 7 * nsino) + table + (1 << 20)
 
 
-class _Solve:
-    """A request's device state: projector, NAG state, the captured graph of its iterations,
-    the buffers the graph starts from and the one it leaves the iterate in."""
-
-    def __init__(self, key, P, nag, graph, u0, y0, u_out, nbytes):
-        self.key, self.P, self.nag, self.graph = key, P, nag, graph
-        self.u0, self.y0, self.u_out, self.nbytes = u0, y0, u_out, nbytes
+def bucket_of(req: Request):
+    return (geometry_key(req.geom), int(req.iters), int(req.power_iters), float(req.lam))
 
 
-class _Active:
-    def __init__(self, req, stream, solve, out_host, done, nbytes):
-        self.req, self.stream, self.solve = req, stream, solve
-        self.out_host, self.done, self.nbytes = out_host, done, nbytes
+class _Batch:
+    """A slot batch of one bucket: projector, slot solver, graphs per occupancy, stream."""
+
+    def __init__(self, bucket, P, nag, stream, lv, plv, capacity, nbytes, dim):
+        self.bucket, self.P, self.nag, self.stream = bucket, P, nag, stream
+        self.lv, self.plv, self.C, self.nbytes, self.dim = lv, plv, capacity, nbytes, dim
+        self.slots = []            # [request, iterations issued, pinned result buffer]
+        self.graphs = {}
+        self.inflight = []         # events of issued iterations
+        self.pending_out = []      # (request, pinned buffer, event) read-outs queued
 
 
 class ReconServer:
-    """budget_bytes: device memory the admitted requests may hold; max_active: requests on
-    the GPU at once; priorities: order streams by request cost (else all at one priority);
+    """budget_bytes: device memory the admitted batches may hold; max_active: batches on the
+    GPU at once; max_slots: requests per batch (2D, 3D); use_graphs: replay captured
+    iterations (else launch them one by one); priorities: order streams by request cost;
     cost_edges: cost thresholds between priority levels (default: decades of
-    ``cost_estimate`` from 1e10, the cheapest level highest); level_caps: requests of each
-    level (highest first) that may run at once; aging: promote requests that waited longer
-    than their estimated service time by one priority level; max_idle: finished solves kept
-    for reuse by later requests of their shape bucket."""
+    ``cost_estimate`` from 1e10, the cheapest level highest); level_caps: batches of each
+    level (highest first) that may run at once; max_idle: emptied batches kept for reuse."""
 
     def __init__(self, device="cuda:0", budget_bytes: int = 120 << 30, max_active: int = 16,
                  use_graphs: bool = True, priorities: bool = True, cost_edges=None, level_caps=None,
-                 aging: bool = True, max_idle: int = 4):
+                 max_idle: int = 4, max_slots=(8, 4), inflight: int = 2):
         self.device = torch.device(device)
         self.budget = int(budget_bytes)
         self.max_active = int(max_active)
         self.use_graphs = use_graphs
+        self.max_slots = tuple(int(v) for v in max_slots)
+        self.inflight = max(1, int(inflight))
         lo, hi = priority_range() if priorities else (0, 0)
         hi = max(hi, lo - 3)                                  # at most four levels
         self.levels = list(range(hi, lo + 1))               # highest priority first
         self.cost_edges = list(cost_edges) if cost_edges is not None else \
             [10.0 ** e for e in range(10, 10 + len(self.levels) - 1)]
-        # one stream per slot and level, created up front so that no two admitted requests
-        # ever share a stream
         self.pool = {lv: [torch.cuda.Stream(device=self.device, priority=lv) for _ in range(self.max_active)]
                      for lv in self.levels}
         if level_caps is None:
@@ -145,14 +141,15 @@ class ReconServer:
             if len(self.levels) > 1:
                 level_caps[-1] = 1
         self.caps = {lv: max(1, min(int(c), self.max_active)) for lv, c in zip(self.levels, level_caps)}
-        self.running = {lv: 0 for lv in self.levels}
-        self.aging = aging
-        self.sec_per_cost = None     # smallest (completion - admission) / cost seen so far
+        self.running = {lv: 0 for lv in self.levels}      # batches (with requests) per level
         self.sigma_cache = {}        # (geometry key, power iterations) -> (||W||^2 on the device, event)
         self.sigma_hits = 0
-        self.max_idle = int(max_idle) if use_graphs else 0
-        self.idle = []               # finished solves kept for reuse, oldest first
-        self.graph_hits = 0
+        self.max_idle = int(max_idle)
+        self.batches = []            # batches holding requests
+        self.idle = []               # emptied batches kept for reuse, oldest first
+        self.joined = 0              # requests that joined a batch already holding requests
+        self.batch_hits = 0          # batches reused from the idle list
+        self.max_occupancy = 0
         self.slots = self.max_active
         self._deferred = []          # projectors released once the device is idle
 
@@ -161,143 +158,120 @@ class ReconServer:
         i = sum(1 for e in self.cost_edges if c >= e)
         return self.levels[min(i, len(self.levels) - 1)]
 
-    def stream_level(self, req: Request, now: float) -> int:
-        """Priority of the request's stream: its class level, one level higher when it has
-        waited longer than its estimated service time."""
-        lv = self.level_of(req)
-        if not self.aging or self.sec_per_cost is None:
-            return lv
-        est = self.sec_per_cost * cost_estimate(req.geom, req.iters, req.power_iters)
-        return self.levels[aged_level(self.levels.index(lv), now - req.arrival, est)]
+    def capacity_of(self, req: Request) -> int:
+        """Slots of a new batch for this request: the per-dimension maximum, fewer when the
+        budget holds fewer request footprints (at least one)."""
+        top = self.max_slots[1] if req.geom.get("dim", 2) == 3 else self.max_slots[0]
+        return max(1, min(top, self.budget // max(footprint_bytes(req.geom), 1)))
+
+    def batch_bytes(self, req: Request) -> int:
+        return self.capacity_of(req) * footprint_bytes(req.geom)
 
     # -----------------------------------------------------------------------------------
-    def _launch(self, req: Request, now: float) -> _Active:
-        lv = self.level_of(req)
-        plv = self.stream_level(req, now)
-        s = self.pool[plv].pop()
-        self.slots -= 1
-        self.running[lv] += 1
-        try:
-            return self._start(req, now, lv, plv, s)
-        except Exception:
-            self.slots += 1
-            self.running[lv] -= 1
-            self.pool[plv].append(s)
-            raise
-
-    def _start(self, req: Request, now: float, lv: int, plv: int, s) -> _Active:
-        g = req.geom
-        bucket = (geometry_key(g), req.iters, req.power_iters, float(req.lam))
-        sv = None
-        for i, cand in enumerate(self.idle):
-            if cand.key == bucket:
-                sv = self.idle.pop(i)
-                break
-        with torch.cuda.device(self.device), torch.cuda.stream(s):
-            data = torch.from_numpy(np.ascontiguousarray(req.sino, dtype=np.float32)).pin_memory()
-            if sv is not None:
-                # same shape bucket: load the data, reset the iterate, replay the graph
-                if data.numel() != sv.nag.p.numel():
-                    raise ValueError("projections of %d values for a geometry of %d" % (data.numel(), sv.nag.p.numel()))
-                sv.nag.p.copy_(data.reshape(sv.nag.p.shape), non_blocking=True)
-                sv.u0.zero_()
-                sv.y0.zero_()
-                sv.graph.replay()
-                self.graph_hits += 1
-            else:
-                sv = self._new_solve(req, bucket, data, s)
-            out_host = torch.empty(tuple(sv.P.vol_shape), dtype=torch.float32).pin_memory()
-            out_host.copy_(sv.u_out[0], non_blocking=True)
-            done = torch.cuda.Event()
-            done.record(s)
-        req.t_admit = now
-        return _Active(req, (lv, plv, s), sv, out_host, done, footprint_bytes(g))
-
-    def _new_solve(self, req: Request, bucket, data, s) -> _Solve:
-        g = req.geom
-        P = Projector(g, device=self.device)
-        p = data.to(self.device, non_blocking=True).reshape((1,) + tuple(P.sino_shape))
-        key = (geometry_key(g), req.power_iters)
+    def _sigma2(self, P, req, s):
+        key = (geometry_key(req.geom), req.power_iters)
         hit = self.sigma_cache.get(key)
         if hit is None:
             gen = torch.Generator(device=self.device)
-            gen.manual_seed(geometry_seed(g))
+            gen.manual_seed(geometry_seed(req.geom))
             start = torch.randn((1,) + tuple(P.vol_shape), generator=gen, device=self.device, dtype=torch.float32)
             sig2 = power_norm2_device(P, iters=req.power_iters, start=start)
             ev = torch.cuda.Event()
             ev.record(s)
             self.sigma_cache[key] = (sig2, ev)
-        else:
-            sig2, ev = hit
-            s.wait_event(ev)
-            sig2.record_stream(s)         # read on this stream too
-            self.sigma_hits += 1
-        # an estimated norm: a 1% margin keeps the step 1 / (1 + lam) below 1 / L
-        nag = NAG(P, 1, lam=req.lam, sigma2_device=sig2, sigma_scale=1.01)
-        nag.start(p)
-        u0, y0 = nag.u, nag.y
-        graph = None
-        if self.use_graphs:
-            graph = torch.cuda.CUDAGraph()
-            graph.capture_begin()
-            for _ in range(req.iters):
-                nag.step()
-            graph.capture_end()
-            graph.replay()
-        else:
-            for _ in range(req.iters):
-                nag.step()
-        return _Solve(bucket, P, nag, graph, u0, y0, nag.u, footprint_bytes(g))
+            return sig2
+        sig2, ev = hit
+        s.wait_event(ev)
+        sig2.record_stream(s)
+        self.sigma_hits += 1
+        return sig2
 
-    def _finish(self, act: _Active, now: float):
-        act.req.result = act.out_host.numpy().copy()
-        act.req.t_done = now
-        self.slots += 1
-        lv, plv, s = act.stream
-        self.pool[plv].append(s)
-        self.running[lv] -= 1
-        spc = (now - act.req.t_admit) / cost_estimate(act.req.geom, act.req.iters, act.req.power_iters)
-        self.sec_per_cost = spc if self.sec_per_cost is None else min(self.sec_per_cost, spc)
-        sv = act.solve
-        act.solve = None
-        if self.max_idle > 0 and sv.graph is not None:
-            self.idle.append(sv)
-            while len(self.idle) > self.max_idle:
-                self._drop(self.idle.pop(0))
-        else:
-            self._drop(sv)
+    def _new_batch(self, req: Request) -> _Batch:
+        lv = self.level_of(req)
+        s = self.pool[lv].pop()
+        try:
+            with torch.cuda.device(self.device), torch.cuda.stream(s):
+                P = Projector(req.geom, device=self.device)
+                sig2 = self._sigma2(P, req, s)
+                C = self.capacity_of(req)
+                nag = NAGSlots(P, C, req.iters, req.lam, sig2, sigma_scale=1.01)
+                nag.reserve()
+        except Exception:
+            self.pool[lv].append(s)
+            raise
+        return _Batch(bucket_of(req), P, nag, s, lv, lv, C, self.batch_bytes(req), req.geom.get("dim", 2))
 
-    def _drop(self, sv: _Solve):
-        self._deferred.append(sv.P)
-        sv.graph = None
-        sv.nag = None
+    def _join(self, b: _Batch, req: Request, now: float):
+        data = torch.from_numpy(np.ascontiguousarray(req.sino, dtype=np.float32))
+        if data.numel() != b.nag.p[0].numel():
+            raise ValueError("projections of %d values for a geometry of %d" % (data.numel(), b.nag.p[0].numel()))
+        with torch.cuda.device(self.device), torch.cuda.stream(b.stream):
+            b.nag.load(len(b.slots), data.pin_memory().to(self.device, non_blocking=True))
+        b.slots.append([req, 0, torch.empty(tuple(b.P.vol_shape), dtype=torch.float32).pin_memory()])
+        req.t_admit = now
+        self.max_occupancy = max(self.max_occupancy, len(b.slots))
 
-    def idle_bytes(self) -> int:
-        return sum(sv.nbytes for sv in self.idle)
+    def _issue(self, b: _Batch):
+        """One iteration of the batch's occupied slots; read-out and compaction of the slots
+        that finish with it."""
+        n = len(b.slots)
+        with torch.cuda.device(self.device), torch.cuda.stream(b.stream):
+            if self.use_graphs:
+                gr = b.graphs.get(n)
+                if gr is None:
+                    gr = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(gr, stream=b.stream):
+                        b.nag.step(n)
+                    b.graphs[n] = gr
+                    # capturing does not run the work: run it once
+                gr.replay()
+            else:
+                b.nag.step(n)
+            ev = torch.cuda.Event()
+            ev.record(b.stream)
+            b.inflight.append(ev)
+            for sl in b.slots:
+                sl[1] += 1
+            for i in reversed(range(n)):
+                req, k, buf = b.slots[i]
+                if k >= req.iters:
+                    buf.copy_(b.nag.u[i], non_blocking=True)
+                    done = torch.cuda.Event()
+                    done.record(b.stream)
+                    b.pending_out.append((req, buf, done))
+                    last = len(b.slots) - 1
+                    if i != last:
+                        b.nag.move(last, i)
+                        b.slots[i] = b.slots[last]
+                    b.slots.pop()
 
     def _memory_blocked(self, pending, now, used) -> bool:
-        """Whether the next request admission would take (the first arrived one whose class
-        has a free slot) waits for memory."""
         for r in pending:
             if r.arrival > now:
+                return False
+            if any(b.bucket == bucket_of(r) and len(b.slots) < b.C for b in self.batches):
                 return False
             lv = self.level_of(r)
             if self.running[lv] >= self.caps[lv]:
                 continue
-            return used + self.idle_bytes() + footprint_bytes(r.geom) > self.budget
+            return used + self.batch_bytes(r) > self.budget
         return False
 
+    def _drop(self, b: _Batch):
+        self._deferred.append(b.P)
+        b.graphs = {}
+        b.nag = None
+
     def _release_deferred(self):
-        # freeing a geometry table synchronises the device; done only when it is idle
         for P in self._deferred:
             P.close()
         self._deferred = []
 
     # -----------------------------------------------------------------------------------
     def serve(self, requests, realtime: bool = True, poll_s: float = 2e-4):
-        """Serve `requests` (sorted by arrival).  With realtime, arrivals follow the wall
-        clock from the start of the call; otherwise every request is available at once.
-        Returns the requests with result, t_admit, t_done filled in (seconds)."""
+        """Serve `requests`.  With realtime, arrivals follow the wall clock from the start of
+        the call; otherwise every request is available at once.  Returns the requests with
+        result, t_admit, t_done filled in (seconds)."""
         pending = sorted(requests, key=lambda r: r.arrival)
         if not realtime:
             for r in pending:
@@ -307,48 +281,95 @@ class ReconServer:
                                                                                        self.budget)
             r.t_done = r.arrival
             pending.remove(r)
-        active = []
         used = 0
         t0 = time.perf_counter()
-        while pending or active:
+        while pending or self.batches:
             now = time.perf_counter() - t0
-            # admit in arrival order while memory and a slot of the request's class are free; idle
-            # solves hold memory too and are released, oldest first, when a request needs it
-            idx = admit_order(pending, now, self.slots, self.running, self.caps, used + self.idle_bytes(),
-                              self.budget, self.level_of, lambda r: footprint_bytes(r.geom))
-            while not idx and self.idle and self.slots > 0 and self._memory_blocked(pending, now, used):
-                self._drop(self.idle.pop(0))
-                idx = admit_order(pending, now, self.slots, self.running, self.caps, used + self.idle_bytes(),
-                                  self.budget, self.level_of, lambda r: footprint_bytes(r.geom))
-            for i in idx:
+            # admissions in arrival order: a free slot of the bucket's batch, else a new batch
+            i = 0
+            while i < len(pending) and pending[i].arrival <= now:
                 req = pending[i]
+                bk = bucket_of(req)
+                target = next((b for b in self.batches if b.bucket == bk and len(b.slots) < b.C), None)
                 try:
-                    active.append(self._launch(req, time.perf_counter() - t0))
-                    used += footprint_bytes(req.geom)
+                    if target is not None:
+                        self._join(target, req, now)
+                        self.joined += 1
+                        pending.pop(i)
+                        continue
+                    reuse = next((j for j, b in enumerate(self.idle) if b.bucket == bk), None)
+                    lv = self.level_of(req)
+                    if self.slots <= 0 or self.running[lv] >= self.caps[lv]:
+                        i += 1
+                        continue
+                    need = 0 if reuse is not None else self.batch_bytes(req)
+                    while (reuse is None and self.idle and
+                           used + self.idle_bytes() + need > self.budget):
+                        self._drop(self.idle.pop(0))
+                    if used + self.idle_bytes() + need > self.budget:
+                        break                                   # waits for memory; later ones wait too
+                    if reuse is not None:
+                        b = self.idle.pop(reuse)
+                        self.batch_hits += 1
+                        b.stream = self.pool[b.lv].pop()
+                    else:
+                        b = self._new_batch(req)
+                    used += b.nbytes
+                    self.slots -= 1
+                    self.running[b.lv] += 1
+                    self.batches.append(b)
+                    self._join(b, req, now)
+                    pending.pop(i)
                 except (CsmError, ValueError, RuntimeError) as e:   # this request cannot run
                     req.error = "%s: %s" % (type(e).__name__, e)
                     req.t_done = time.perf_counter() - t0
-            for i in reversed(idx):
-                pending.pop(i)
-            # completions
+                    pending.pop(i)
+            # iterations: at most `inflight` per batch queued on the GPU
+            issued = False
+            for b in self.batches:
+                b.inflight = [e for e in b.inflight if not e.query()]
+                if b.slots and len(b.inflight) < self.inflight:
+                    self._issue(b)
+                    issued = True
+            # results
             still = []
-            for act in active:
-                if act.done.query():
-                    self._finish(act, time.perf_counter() - t0)
-                    used -= act.nbytes
+            for b in self.batches:
+                keep = []
+                for req, buf, done in b.pending_out:
+                    if done.query():
+                        req.result = buf.numpy().copy()
+                        req.t_done = time.perf_counter() - t0
+                    else:
+                        keep.append((req, buf, done))
+                b.pending_out = keep
+                if not b.slots and not b.pending_out:
+                    b.inflight = []
+                    self.pool[b.lv].append(b.stream)
+                    self.slots += 1
+                    self.running[b.lv] -= 1
+                    used -= b.nbytes
+                    if self.use_graphs and self.max_idle > 0:
+                        self.idle.append(b)
+                        while len(self.idle) > self.max_idle:
+                            self._drop(self.idle.pop(0))
+                    else:
+                        self._drop(b)
                 else:
-                    still.append(act)
-            active = still
-            if not active and self._deferred:
+                    still.append(b)
+            self.batches = still
+            if not self.batches and self._deferred:
                 self._release_deferred()
-            if active or pending:
+            if not issued and (self.batches or pending):
                 time.sleep(poll_s)
         torch.cuda.synchronize(self.device)
         self._release_deferred()
         return requests
 
+    def idle_bytes(self) -> int:
+        return sum(b.nbytes for b in self.idle)
+
     def close(self):
-        """Release the idle solves and their geometry tables."""
+        """Release the idle batches and their geometry tables."""
         while self.idle:
             self._drop(self.idle.pop(0))
         torch.cuda.synchronize(self.device)
@@ -370,6 +391,29 @@ def solve_alone(req: Request, device="cuda:0") -> np.ndarray:
     out = u[0].cpu().numpy().copy()
     P.close()
     return out
+
+
+def serve_unbatched(requests, device="cuda:0", realtime: bool = True):
+    """The unbatched reference server, run for real: requests one at a time in arrival order
+    with plain calls (solve_alone), waiting for each arrival on the wall clock.  Fills result,
+    t_admit and t_done like ReconServer.serve."""
+    pending = sorted(requests, key=lambda r: r.arrival)
+    if not realtime:
+        for r in pending:
+            r.arrival = 0.0
+    t0 = time.perf_counter()
+    for r in pending:
+        now = time.perf_counter() - t0
+        if r.arrival > now:
+            time.sleep(r.arrival - now)
+        r.t_admit = time.perf_counter() - t0
+        try:
+            r.result = solve_alone(r, device=device)
+        except (CsmError, ValueError, RuntimeError) as e:
+            r.error = "%s: %s" % (type(e).__name__, e)
+        torch.cuda.synchronize(torch.device(device))
+        r.t_done = time.perf_counter() - t0
+    return requests
 
 
 def latency_stats(lat):

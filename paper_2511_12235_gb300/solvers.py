@@ -226,3 +226,77 @@ class NAG:
                 if float(gn.max().item()) < tol:
                     break
         return self.u
+
+
+def fista_thetas(iters: int):
+    """theta_k = (t_k - 1) / t_{k+1} for k = 0 .. iters - 1, t_0 = 1 (the momentum sequence of
+    NAG.step, in the same FP64 arithmetic)."""
+    t, out = 1.0, []
+    for _ in range(iters):
+        t_new = 0.5 * (1.0 + math.sqrt(1.0 + 4.0 * t * t))
+        out.append((t - 1.0) / t_new)
+        t = t_new
+    return out
+
+
+class NAGSlots:
+    """NAG (as ``NAG``) on a batch of slots whose problems share W, lambda and sigma but are at
+    different iterations: slot b runs its own momentum sequence (csm_fista_coeffs reads its
+    iteration counter on the device).  ``step(n)`` advances slots 0 .. n - 1 by one iteration
+    in fixed buffers (no host values enter it), so it can be captured once per n in a CUDA
+    graph and replayed while problems are loaded into free slots and finished ones are read
+    out and compacted.  A slot's iterates equal those of ``NAG`` on its problem alone."""
+
+    def __init__(self, P: Projector, capacity: int, iters: int, lam: float, sigma2_device: torch.Tensor,
+                 sigma_scale: float = 1.0, dtype: torch.dtype = torch.float32):
+        self.P, self.C, self.iters, self.lam, self.dtype = P, capacity, iters, float(lam), dtype
+        dev = P.device
+        vs, ss = (capacity,) + tuple(P.vol_shape), (capacity,) + tuple(P.sino_shape)
+        self.u = torch.zeros(vs, dtype=dtype, device=dev)
+        self.y = torch.zeros(vs, dtype=dtype, device=dev)
+        self.g = torch.zeros(vs, dtype=dtype, device=dev)
+        self.r = torch.zeros(ss, dtype=dtype, device=dev)
+        self.p = torch.zeros(ss, dtype=dtype, device=dev)
+        self.k = torch.zeros(capacity, dtype=torch.int32, device=dev)
+        self.opt = torch.zeros(capacity, dtype=torch.float64, device=dev)
+        self.th = torch.zeros(capacity, dtype=torch.float64, device=dev)
+        self.table = torch.tensor(fista_thetas(iters), dtype=torch.float64, device=dev)
+        s2 = sigma2_device.to(device=dev, dtype=torch.float64).reshape(-1)
+        self.sig2 = (s2.expand(capacity) if s2.numel() == 1 else s2).contiguous()
+        self.inv_c = 1.0 / sigma_scale
+        self.ops = VecOps(dev, capacity)
+
+    def reserve(self):
+        """Allocates the projector workspaces of every batch size up front (before capture)."""
+        self.P.workspace(0, self.C, self.dtype)
+        self.P.workspace(1, self.C, self.dtype)
+
+    def load(self, slot: int, p: torch.Tensor):
+        """Puts a problem (its projections) into a free slot, iterate zero, iteration 0."""
+        self.p[slot].copy_(p.reshape(self.p.shape[1:]), non_blocking=True)
+        self.u[slot].zero_()
+        self.y[slot].zero_()
+        self.k[slot:slot + 1].zero_()
+
+    def move(self, src: int, dst: int):
+        """Moves a slot's problem and state to another slot (compaction)."""
+        for t in (self.u, self.y, self.p, self.k):
+            t[dst].copy_(t[src])
+
+    def step(self, n: int):
+        with nvtx_range("nag_slots_step"):
+            P, ops, inv = self.P, self.ops, self.inv_c
+            u, y, g, r, p = self.u[:n], self.y[:n], self.g[:n], self.r[:n], self.p[:n]
+            sd = self.sig2[:n]
+            step = 1.0 / (1.0 + self.lam)
+            P.forward(y, out=r)
+            ops.axpby(-1.0, p, inv, r, b_den=sd, flags=2)             # r = W y / sigma - p
+            P.back(r, out=g)
+            ops.axpby(self.lam, y, inv, g, b_den=sd, flags=2)         # g = grad F(y)
+            ops.axpby(1.0, y, -step, g)                               # g = u_new = y - step grad
+            capi.csm_fista_coeffs(n, self.table.data_ptr(), self.table.numel(), self.k.data_ptr(),
+                                  self.opt.data_ptr(), self.th.data_ptr(),
+                                  torch.cuda.current_stream(P.device).cuda_stream)
+            ops.axpby(1.0, u, 0.0, y)                                 # y = u_old
+            ops.axpby(1.0, g, -1.0, y, a_num=self.opt, b_num=self.th)  # y = (1 + theta) u_new - theta u_old
+            ops.axpby(1.0, g, 0.0, u)                                 # u = u_new

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "CONFIGS", "geometry", "uniform_angles", "ellipse_phantom", "ellipsoid_phantom",
-    "poisson_sinogram", "serving_requests",
+    "poisson_sinogram", "serving_requests", "serving_geometry",
 ]
 
 
@@ -218,13 +218,30 @@ def poisson_sinogram(p: np.ndarray, seed: int, photons: float = 1e5, max_line: f
     return noisy.astype(p.dtype), kappa
 
 
+SERVING_PROTOCOLS_2D = ((256, 360), (512, 720), (768, 1080), (1024, 1440))
+SERVING_PROTOCOLS_3D = ((64, 90), (128, 180), (192, 270), (256, 360))
+
+
+def serving_geometry(n: int, n_views: int, dim: int) -> dict:
+    """The serving mix's geometry for grid side n: s = 1.953 n, source-detector 2.930 n (the
+    512-grid ratios), unit voxels and elements, detector 1.5 n (2D) / 1.5 n x 1.5 n (3D)."""
+    nd = int(round(1.5 * n))
+    nd += nd % 2
+    if dim == 2:
+        return geometry(n, n, 1, n_views=n_views, s=1.953 * n, sdd=2.930 * n, nu=nd)
+    g = geometry(n, n, n, n_views=n_views, s=1.953 * n, sdd=2.930 * n, nu=nd, nv=nd)
+    g["dim"] = 3
+    return g
+
+
 def serving_requests(n_requests: int, seed: int, rate_per_s: float):
     """Poisson arrivals of reconstruction requests for the serving mix.
 
-    60% 2D (grid N in U{256..1024}, views in U{360..1440}, nu = 1.5 N) and 40% 3D
-    (N in U{64..256}, views in U{90..360}, detector 1.5N x 1.5N).  Geometry follows the
-    512-grid ratios: s = 1.953 N, source-detector = 2.930 N, unit voxels and elements.
-    Each request carries a phantom seed.  Returns a list of dicts with arrival times.
+    60% 2D, 40% 3D, each request on one of a scanner's fixed protocols (grid side and views):
+    2D N in {256, 512, 768, 1024} with 360 .. 1440 views, 3D N in {64, 128, 192, 256} with
+    90 .. 360 views (SERVING_PROTOCOLS_*), chosen uniformly; the geometry of serving_geometry.
+    Requests of one protocol share the geometry, as on a scanner.  Each request carries a
+    phantom seed.  Returns a list of dicts with arrival times.
     """
     rng = np.random.default_rng(seed)
     t = 0.0
@@ -232,19 +249,10 @@ def serving_requests(n_requests: int, seed: int, rate_per_s: float):
     for i in range(n_requests):
         t += rng.exponential(1.0 / rate_per_s)
         if rng.uniform() < 0.6:
-            n = int(rng.integers(256, 1025))
-            n -= n % 2
-            nviews = int(rng.integers(360, 1441))
-            nu = int(round(1.5 * n))
-            nu += nu % 2
-            g = geometry(n, n, 1, n_views=nviews, s=1.953 * n, sdd=2.930 * n, nu=nu)
+            n, nv = SERVING_PROTOCOLS_2D[int(rng.integers(0, len(SERVING_PROTOCOLS_2D)))]
+            g = serving_geometry(n, nv, 2)
         else:
-            n = int(rng.integers(64, 257))
-            n -= n % 2
-            nviews = int(rng.integers(90, 361))
-            nd = int(round(1.5 * n))
-            nd += nd % 2
-            g = geometry(n, n, n, n_views=nviews, s=1.953 * n, sdd=2.930 * n, nu=nd, nv=nd)
-            g["dim"] = 3
+            n, nv = SERVING_PROTOCOLS_3D[int(rng.integers(0, len(SERVING_PROTOCOLS_3D)))]
+            g = serving_geometry(n, nv, 3)
         out.append(dict(id=i, arrival=t, geom=g, seed=int(rng.integers(0, 2**31 - 1))))
     return out
