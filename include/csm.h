@@ -210,6 +210,29 @@ csm_status csm_dot_noalloc(const void* a, const void* c, int64_t n, int64_t batc
 csm_status csm_fma_rate(csm_dtype dt, int64_t iters, int blocks_per_sm, int launches,
                         double* flops, double* seconds, void* cuda_stream);
 
+/* ---- line-based comparator projectors ----------------------------------------------------
+ * The line-integration system matrices the paper compares the consistent one with (Section
+ * "Related work": Siddon's and Joseph's methods among the line-based approaches; Section
+ * "Computational complexity": "several lines per detector element, averaged"), on the same
+ * geometry handle and layouts as csm_forward / csm_back:
+ *   CSM_LINE_SIDDON  W_ij = length of the ray inside voxel j;
+ *   CSM_LINE_JOSEPH  the ray sampled at the centre plane of every voxel slice along its major
+ *                    axis, the volume interpolated linearly (2D) / bilinearly (3D) between
+ *                    the voxel centres of the slice, weighted by the ray length per slice.
+ * An element's value is the mean over `lines` rays (lines x lines in 3D) from the source to
+ * evenly spaced points of the element, u = u_k + (m + 1/2) du / lines (1 <= lines <= 64).
+ * csm_back_line is the exact adjoint of csm_forward_line (the same rays and weights), added
+ * into x with atomics: x must be CSM_F32 or CSM_F64 (else CSM_EUNSUPPORTED); its FP sums are
+ * in no fixed order.  flags: CSM_ACCUMULATE.  No workspace; asynchronous on the stream. */
+#define CSM_LINE_SIDDON 1
+#define CSM_LINE_JOSEPH 2
+csm_status csm_forward_line(csm_geom_t geom, int model, int lines, const void* x, void* p,
+                            int64_t batch, csm_dtype x_dt, csm_dtype p_dt, int flags,
+                            void* cuda_stream);
+csm_status csm_back_line(csm_geom_t geom, int model, int lines, const void* p, void* x,
+                         int64_t batch, csm_dtype p_dt, csm_dtype x_dt, int flags,
+                         void* cuda_stream);
+
 /* ---- the system matrix as an explicit sparse matrix -------------------------------------
  * The paper writes the reconstruction problem with W as a matrix (Introduction, Eq. (ip):
  * p = W u) and names the algebraic row-action methods (ART, SART) among the reconstruction

@@ -88,6 +88,8 @@ def _load():
         lib.orc3d_coo.restype = C.c_long
         lib.orc3d_back_slab.argtypes = [gp, dp, dp, ip, C.c_int, C.c_int, C.c_int]
         lib.orc3d_back_slab.restype = C.c_long
+        lib.orc_line_forward.argtypes = [gp, C.c_int, C.c_int, dp, dp, ip, C.c_int]
+        lib.orc_line_back.argtypes = [gp, C.c_int, C.c_int, dp, dp, ip, C.c_int]
         lib.orc2d_count.argtypes = [gp, ip, C.c_int]
         lib.orc2d_count.restype = C.c_long
         lib.orc_num_threads.restype = C.c_int
@@ -267,3 +269,28 @@ def coo(g: dict, views=None, cap: int | None = None):
     if n < 0:
         raise RuntimeError("COO capacity too small")
     return rows[:n].copy(), cols[:n].copy(), vals[:n].copy()
+
+
+LINE_MODELS = {"siddon": 1, "joseph": 2}
+
+
+def line_forward(g: dict, x: np.ndarray, model: str = "siddon", lines: int = 1, views=None) -> np.ndarray:
+    """Line-based comparator projections (Siddon: lengths in voxels; Joseph: interpolation
+    per slice), the mean over `lines` rays per element (lines x lines in 3D).  Returns
+    [views][nu] (2D) or [views][nv][nu] (3D)."""
+    h = _GeomHolder(g)
+    v = _views(g, views)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    p = np.zeros((len(v), g["nv"], g["nu"]), np.float64)
+    _load().orc_line_forward(h.ref, LINE_MODELS[model], int(lines), _dptr(x), _dptr(p), _iptr(v), len(v))
+    return p if g.get("dim", 2) == 3 else p[:, 0, :]
+
+
+def line_back(g: dict, p: np.ndarray, model: str = "siddon", lines: int = 1, views=None) -> np.ndarray:
+    """The adjoint of line_forward (same rays and weights)."""
+    h = _GeomHolder(g)
+    v = _views(g, views)
+    p = np.ascontiguousarray(np.asarray(p, np.float64).reshape(len(v), g["nv"], g["nu"]))
+    x = np.zeros((g["nz"], g["ny"], g["nx"]), np.float64)
+    _load().orc_line_back(h.ref, LINE_MODELS[model], int(lines), _dptr(p), _dptr(x), _iptr(v), len(v))
+    return x if g.get("dim", 2) == 3 else x[0]

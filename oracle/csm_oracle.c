@@ -580,6 +580,159 @@ long orc2d_coo(const orc_geom* g, const int* views, int nsel, int* rows, int* co
     return cnt;
 }
 
+/* ----------------------------------------------------------------------------------------
+ * Line-based comparator matrices (Section "Related work": line-integration methods; Section
+ * "Computational complexity": several lines per detector element, averaged).  A ray goes from
+ * the source S to the detector point D = S - sdd e_s + u e_u + w e_z of view phi; an
+ * element's value is the mean over `lines` rays to u = u_k + (m + 1/2) du / lines (and, in 3D,
+ * lines x lines rays with w = v_l + (n + 1/2) dv / lines).
+ *   Siddon: the line integral of the piecewise-constant image, i.e. the sum over voxels of the
+ *     length of the ray inside each, found as in Siddon's method: every crossing parameter of
+ *     the ray with a grid plane, sorted; between consecutive crossings the ray is inside the
+ *     voxel that contains the midpoint.
+ *   Joseph: the ray sampled at the centre plane of every voxel slice along its major axis,
+ *     the image interpolated (linearly in 2D, bilinearly in 3D, zero outside the grid) between
+ *     the voxel centres of that slice, each sample weighted by the ray length per slice.
+ * 2D when nz == 1 and nv == 1 (z and w ignored).
+ * ---------------------------------------------------------------------------------------- */
+static int cmp_double(const void* a, const void* b) {
+    double x = *(const double*)a, y = *(const double*)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* visit(voxel index, weight) for every voxel the ray meets; ctx passed through */
+typedef void (*ray_visit)(void* ctx, size_t vox, double w);
+
+static void ray_siddon(const orc_geom* g, const double S[3], const double d[3], int is3d, ray_visit f, void* ctx) {
+    double lo[3] = {grid_x(g, 0), grid_y(g, 0), grid_z(g, 0)};
+    double hi[3] = {grid_x(g, g->nx), grid_y(g, g->ny), grid_z(g, g->nz)};
+    int n[3] = {g->nx, g->ny, g->nz};
+    double h[3] = {g->a, g->b, g->c};
+    int dims = is3d ? 3 : 2;
+    int cap = g->nx + g->ny + (is3d ? g->nz : 0) + 8;
+    double* al = (double*)malloc(sizeof(double) * cap);
+    int na = 0;
+    al[na++] = 0.0;
+    al[na++] = 1.0;
+    for (int a = 0; a < dims; ++a) {
+        if (d[a] == 0.0) continue;
+        for (int i = 0; i <= n[a]; ++i) {
+            double t = (lo[a] + i * h[a] - S[a]) / d[a];
+            if (t > 0.0 && t < 1.0 && na < cap) al[na++] = t;
+        }
+    }
+    qsort(al, na, sizeof(double), cmp_double);
+    double len = sqrt(d[0] * d[0] + d[1] * d[1] + (is3d ? d[2] * d[2] : 0.0));
+    for (int m = 0; m + 1 < na; ++m) {
+        double t0 = al[m], t1 = al[m + 1];
+        if (!(t1 > t0)) continue;
+        double tm = 0.5 * (t0 + t1);
+        int idx[3] = {0, 0, 0};
+        int inside = 1;
+        for (int a = 0; a < dims; ++a) {
+            double q = S[a] + tm * d[a];
+            if (q < lo[a] || q > hi[a]) { inside = 0; break; }
+            int i = (int)floor((q - lo[a]) / h[a]);
+            if (i < 0 || i >= n[a]) { inside = 0; break; }
+            idx[a] = i;
+        }
+        if (!inside) continue;
+        f(ctx, ((size_t)idx[2] * g->ny + idx[1]) * g->nx + idx[0], (t1 - t0) * len);
+    }
+    free(al);
+}
+
+static void ray_joseph(const orc_geom* g, const double S[3], const double d[3], int is3d, ray_visit f, void* ctx) {
+    double org[3] = {grid_x(g, 0), grid_y(g, 0), grid_z(g, 0)};
+    double h[3] = {g->a, g->b, g->c};
+    int n[3] = {g->nx, g->ny, g->nz};
+    int m = 0;
+    if (fabs(d[1]) > fabs(d[m])) m = 1;
+    if (is3d && fabs(d[2]) > fabs(d[m])) m = 2;
+    int others[2], no = 0;
+    for (int a = 0; a < (is3d ? 3 : 2); ++a) if (a != m) others[no++] = a;
+    double len = sqrt(d[0] * d[0] + d[1] * d[1] + (is3d ? d[2] * d[2] : 0.0));
+    double wstep = h[m] * len / fabs(d[m]);
+    for (int i = 0; i < n[m]; ++i) {
+        double cm = org[m] + (i + 0.5) * h[m];
+        double t = (cm - S[m]) / d[m];
+        if (t < 0.0 || t > 1.0) continue;
+        /* position of the sample in voxel-centre units along the other axes */
+        double pos[2] = {0.0, 0.0};
+        int base[2] = {0, 0};
+        for (int o = 0; o < no; ++o) {
+            int a = others[o];
+            pos[o] = (S[a] + t * d[a] - org[a]) / h[a] - 0.5;
+            base[o] = (int)floor(pos[o]);
+        }
+        int corners = no == 2 ? 4 : 2;
+        for (int cidx = 0; cidx < corners; ++cidx) {
+            int idx[3] = {0, 0, 0};
+            double w = wstep;
+            int ok = 1;
+            idx[m] = i;
+            for (int o = 0; o < no; ++o) {
+                int bit = (cidx >> o) & 1;
+                int j = base[o] + bit;
+                double fr = pos[o] - base[o];
+                w *= bit ? fr : 1.0 - fr;
+                if (j < 0 || j >= n[others[o]]) ok = 0;
+                idx[others[o]] = j;
+            }
+            if (ok && w != 0.0) f(ctx, ((size_t)idx[2] * g->ny + idx[1]) * g->nx + idx[0], w);
+        }
+    }
+}
+
+typedef struct { const double* x; double acc; } fwd_ctx;
+static void fwd_visit(void* c, size_t vox, double w) { fwd_ctx* k = (fwd_ctx*)c; k->acc += w * k->x[vox]; }
+typedef struct { double* x; double val; } back_ctx;
+static void back_visit(void* c, size_t vox, double w) { back_ctx* k = (back_ctx*)c; k->x[vox] += w * k->val; }
+
+static void element_rays(const orc_geom* g, int model, int lines, int view, int k, int l, ray_visit f, void* ctx) {
+    int is3d = !(g->nz == 1 && g->nv == 1);
+    double phi = g->angles[view], c = cos(phi), sn = sin(phi);
+    int lz = is3d ? lines : 1;
+    for (int mz = 0; mz < lz; ++mz) {
+        double w = is3d ? corner_v(g, l) + (mz + 0.5) / lz * g->dv : 0.0;
+        for (int mu = 0; mu < lines; ++mu) {
+            double u = corner_u(g, k) + (mu + 0.5) / lines * g->du;
+            double S[3] = {g->s * c, g->s * sn, 0.0};
+            double d[3] = {-g->sdd * c - u * sn, -g->sdd * sn + u * c, w};
+            if (model == 1) ray_siddon(g, S, d, is3d, f, ctx);
+            else ray_joseph(g, S, d, is3d, f, ctx);
+        }
+    }
+}
+
+/* p[vi][nv][nu] = mean over each element's rays of the line integrals of x */
+void orc_line_forward(const orc_geom* g, int model, int lines, const double* x, double* p, const int* views, int nsel) {
+    int is3d = !(g->nz == 1 && g->nv == 1);
+    double norm = 1.0 / (lines * (is3d ? lines : 1));
+    #pragma omp parallel for schedule(dynamic, 1) collapse(2)
+    for (int vi = 0; vi < nsel; ++vi)
+        for (int l = 0; l < g->nv; ++l)
+            for (int k = 0; k < g->nu; ++k) {
+                fwd_ctx ctx = {x, 0.0};
+                element_rays(g, model, lines, views[vi], k, l, fwd_visit, &ctx);
+                p[((size_t)vi * g->nv + l) * g->nu + k] = ctx.acc * norm;
+            }
+}
+
+/* x = the adjoint of orc_line_forward applied to p (serial: plain sums) */
+void orc_line_back(const orc_geom* g, int model, int lines, const double* p, double* x, const int* views, int nsel) {
+    int is3d = !(g->nz == 1 && g->nv == 1);
+    double norm = 1.0 / (lines * (is3d ? lines : 1));
+    size_t nvox = (size_t)g->nx * g->ny * g->nz;
+    for (size_t i = 0; i < nvox; ++i) x[i] = 0.0;
+    for (int vi = 0; vi < nsel; ++vi)
+        for (int l = 0; l < g->nv; ++l)
+            for (int k = 0; k < g->nu; ++k) {
+                back_ctx ctx = {x, p[((size_t)vi * g->nv + l) * g->nu + k] * norm};
+                if (ctx.val != 0.0) element_rays(g, model, lines, views[vi], k, l, back_visit, &ctx);
+            }
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

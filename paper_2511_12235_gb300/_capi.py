@@ -24,6 +24,8 @@ CSM_ACCUMULATE = 1
 CSM_RELATIVE_WEIGHTS = 2
 CSM_VOXEL_DRIVEN = 4
 CSM_EXPORT_TRANSPOSE = 8
+CSM_LINE_SIDDON = 1
+CSM_LINE_JOSEPH = 2
 
 
 class csm_geom2d_desc(C.Structure):
@@ -73,6 +75,12 @@ lib.csm_dot_noalloc.restype = _st
 lib.csm_fma_rate.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.c_void_p]
 lib.csm_fma_rate.restype = _st
+lib.csm_forward_line.argtypes = [csm_geom_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                                 C.c_int, C.c_void_p]
+lib.csm_forward_line.restype = _st
+lib.csm_back_line.argtypes = [csm_geom_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int,
+                              C.c_int, C.c_void_p]
+lib.csm_back_line.restype = _st
 lib.csm_export_workspace_bytes.argtypes = [csm_geom_t, C.c_int, C.POINTER(C.c_size_t)]
 lib.csm_export_workspace_bytes.restype = _st
 lib.csm_export_csr.argtypes = [csm_geom_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
@@ -99,7 +107,7 @@ EXPORTED = [
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
     "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
     "csm_fma_rate", "csm_export_workspace_bytes", "csm_export_csr", "csm_csr_spmv", "csm_csr_normalize_rows",
-    "csm_ediv", "csm_fista_coeffs",
+    "csm_ediv", "csm_fista_coeffs", "csm_forward_line", "csm_back_line",
 ]
 CSM_DOT_NOALLOC_MAX_BATCH = 64
 
@@ -215,3 +223,11 @@ def csm_ediv(n, dt, num, den, out, stream) -> None:
 
 def csm_fista_coeffs(batch, table, n_table, k, one_plus, theta, stream) -> None:
     check(lib.csm_fista_coeffs(batch, table, n_table, k, one_plus, theta, stream), "csm_fista_coeffs")
+
+
+def csm_forward_line(h, model, lines, x_ptr, p_ptr, batch, x_dt, p_dt, flags, stream) -> None:
+    check(lib.csm_forward_line(h, model, lines, x_ptr, p_ptr, batch, x_dt, p_dt, flags, stream), "csm_forward_line")
+
+
+def csm_back_line(h, model, lines, p_ptr, x_ptr, batch, p_dt, x_dt, flags, stream) -> None:
+    check(lib.csm_back_line(h, model, lines, p_ptr, x_ptr, batch, p_dt, x_dt, flags, stream), "csm_back_line")

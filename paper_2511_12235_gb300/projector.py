@@ -28,6 +28,9 @@ _DT = {torch.float32: capi.CSM_F32, torch.float64: capi.CSM_F64,
        torch.bfloat16: capi.CSM_BF16, torch.float16: capi.CSM_F16}
 
 
+_LINE = {"siddon": capi.CSM_LINE_SIDDON, "joseph": capi.CSM_LINE_JOSEPH}
+
+
 def _dt(t: torch.dtype) -> int:
     try:
         return _DT[t]
@@ -147,6 +150,36 @@ class Projector:
         with nvtx_range("csm_back"):
             capi.csm_back(self.handle, pb.data_ptr(), out.data_ptr(), B, _dt(pb.dtype), _dt(out.dtype), flags,
                           ws.data_ptr(), ws.numel(), stream)
+        return out[0] if single else out
+
+    def forward_line(self, x: torch.Tensor, model: str = "siddon", lines: int = 1,
+                     out: torch.Tensor | None = None) -> torch.Tensor:
+        """p = W_line x for a line-based comparator model ("siddon" or "joseph"), the mean over
+        `lines` rays per detector element (lines x lines in 3D)."""
+        xb, single = self._batched(x, self.vol_shape)
+        xb = xb.contiguous()
+        B = xb.shape[0]
+        if out is None:
+            out = torch.empty((B,) + tuple(self.sino_shape), dtype=x.dtype, device=self.device)
+        else:
+            out = out.view((B,) + tuple(self.sino_shape))
+        capi.csm_forward_line(self.handle, _LINE[model], lines, xb.data_ptr(), out.data_ptr(), B, _dt(xb.dtype),
+                              _dt(out.dtype), 0, torch.cuda.current_stream(self.device).cuda_stream)
+        return out[0] if single else out
+
+    def back_line(self, p: torch.Tensor, model: str = "siddon", lines: int = 1,
+                  out: torch.Tensor | None = None) -> torch.Tensor:
+        """x = W_line^T p, the exact adjoint of forward_line (float32 / float64 output)."""
+        pb, single = self._batched(p, self.sino_shape)
+        pb = pb.contiguous()
+        B = pb.shape[0]
+        if out is None:
+            odt = pb.dtype if pb.dtype in (torch.float32, torch.float64) else torch.float32
+            out = torch.empty((B,) + tuple(self.vol_shape), dtype=odt, device=self.device)
+        else:
+            out = out.view((B,) + tuple(self.vol_shape))
+        capi.csm_back_line(self.handle, _LINE[model], lines, pb.data_ptr(), out.data_ptr(), B, _dt(pb.dtype),
+                           _dt(out.dtype), 0, torch.cuda.current_stream(self.device).cuda_stream)
         return out[0] if single else out
 
     def nnz(self) -> int:
