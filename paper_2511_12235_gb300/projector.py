@@ -52,6 +52,8 @@ class Projector:
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if self.device.type != "cuda":
             raise ValueError("Projector needs a CUDA device")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         ang = np.ascontiguousarray(np.asarray(geom["angles"], dtype=np.float64))
         self._angles = ang
         aptr = ang.ctypes.data_as(C.POINTER(C.c_double))
