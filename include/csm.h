@@ -105,6 +105,17 @@ csm_status csm_geom_create_3d(const csm_geom3d_desc* desc, csm_geom_t* out);
  * device that holds it and the caller's current device is restored).  NULL is ignored. */
 void csm_geom_free(csm_geom_t geom);
 
+/* Per-element detector sensitivity weights (gains), the measurement model p_i = w_i (W x)_i
+ * (the paper's element-wise measurement of Section "Notation and Setup" with a detector whose
+ * elements respond differently).  weights: host array of n_views x nv x nu values (nv = 1 in
+ * 2D) in the layout of p, finite; NULL removes them (all 1).  From then on csm_forward
+ * multiplies each element's value by its weight, csm_back projects diag(w) p (so it stays
+ * the adjoint), and csm_export_csr scales the rows of W; csm_nnz and the line-based
+ * comparators are unaffected.  Copies the weights to memory owned by the geometry on its
+ * device (synchronous).  Errors: CSM_EINVAL (NULL geometry, non-finite weight, another device
+ * current), CSM_ENOMEM, CSM_ECUDA. */
+csm_status csm_geom_set_element_weights(csm_geom_t geom, const double* weights);
+
 /* Bytes of caller-provided device workspace that csm_forward / csm_back need for this
  * geometry, batch and arithmetic type (op: 0 = forward, 1 = back).  The workspace holds
  * the batch-interleaved copies of the input that the kernels gather from. */

@@ -50,6 +50,8 @@ lib.csm_geom_create_2d.argtypes = [C.POINTER(csm_geom2d_desc), C.POINTER(csm_geo
 lib.csm_geom_create_2d.restype = _st
 lib.csm_geom_create_3d.argtypes = [C.POINTER(csm_geom3d_desc), C.POINTER(csm_geom_t)]
 lib.csm_geom_create_3d.restype = _st
+lib.csm_geom_set_element_weights.argtypes = [csm_geom_t, C.c_void_p]
+lib.csm_geom_set_element_weights.restype = _st
 lib.csm_geom_free.argtypes = [csm_geom_t]
 lib.csm_geom_free.restype = None
 lib.csm_workspace_bytes.argtypes = [csm_geom_t, C.c_int, C.c_int64, C.c_int, C.POINTER(C.c_size_t)]
@@ -107,7 +109,7 @@ EXPORTED = [
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
     "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
     "csm_fma_rate", "csm_export_workspace_bytes", "csm_export_csr", "csm_csr_spmv", "csm_csr_normalize_rows",
-    "csm_ediv", "csm_fista_coeffs", "csm_forward_line", "csm_back_line",
+    "csm_ediv", "csm_fista_coeffs", "csm_forward_line", "csm_back_line", "csm_geom_set_element_weights",
 ]
 CSM_DOT_NOALLOC_MAX_BATCH = 64
 
@@ -231,3 +233,7 @@ def csm_forward_line(h, model, lines, x_ptr, p_ptr, batch, x_dt, p_dt, flags, st
 
 def csm_back_line(h, model, lines, p_ptr, x_ptr, batch, p_dt, x_dt, flags, stream) -> None:
     check(lib.csm_back_line(h, model, lines, p_ptr, x_ptr, batch, p_dt, x_dt, flags, stream), "csm_back_line")
+
+
+def csm_geom_set_element_weights(h, weights_ptr) -> None:
+    check(lib.csm_geom_set_element_weights(h, weights_ptr), "csm_geom_set_element_weights")

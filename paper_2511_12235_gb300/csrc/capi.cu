@@ -48,6 +48,9 @@ Geo make_geo(const csm_geom_s* g) {
     o.rowq4 = g->t.rowq4;
     o.colt_fx = g->t.colt_fx;
     o.colt_d = g->t.colt_d;
+    const size_t nel = (size_t)g->n_views * g->nv * g->nu;
+    o.ew_f = g->w_block ? (const float*)g->w_block : nullptr;
+    o.ew_d = g->w_block ? (const double*)((const char*)g->w_block + ((nel * sizeof(float) + 255) & ~(size_t)255)) : nullptr;
     return o;
 }
 
@@ -341,15 +344,49 @@ csm_status csm_geom_create_3d(const csm_geom3d_desc* d, csm_geom_t* out) {
 
 void csm_geom_free(csm_geom_t g) {
     if (!g) return;
-    if (g->d_block) {
+    if (g->d_block || g->w_block) {
         // release the table on the device that holds it, then restore the caller's device
         int prev = -1;
         const bool have_prev = cudaGetDevice(&prev) == cudaSuccess;
         if (have_prev && prev != g->device) cudaSetDevice(g->device);
-        cudaFree(g->d_block);
+        if (g->d_block) cudaFree(g->d_block);
+        if (g->w_block) cudaFree(g->w_block);
         if (have_prev && prev != g->device) cudaSetDevice(prev);
     }
     delete g;
+}
+
+csm_status csm_geom_set_element_weights(csm_geom_t g, const double* weights) {
+    if (!g) return CSM_EINVAL;
+    csm_status dv = check_device(g);
+    if (dv != CSM_OK) return dv;
+    const size_t nel = (size_t)g->n_views * g->nv * g->nu;
+    if (!weights) {
+        if (g->w_block) {
+            cudaError_t e = cudaFree(g->w_block);
+            g->w_block = nullptr;
+            if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+        }
+        return CSM_OK;
+    }
+    for (size_t i = 0; i < nel; ++i)
+        if (!std::isfinite(weights[i])) return CSM_EINVAL;
+    const size_t of = (nel * sizeof(float) + 255) & ~(size_t)255;
+    std::vector<char> host(of + nel * sizeof(double));
+    float* wf = (float*)host.data();
+    for (size_t i = 0; i < nel; ++i) wf[i] = (float)weights[i];
+    memcpy(host.data() + of, weights, nel * sizeof(double));
+    if (!g->w_block) {
+        cudaError_t e = cudaMalloc(&g->w_block, host.size());
+        if (e != cudaSuccess) {
+            g->w_block = nullptr;
+            set_cuda_error(e);
+            return e == cudaErrorMemoryAllocation ? CSM_ENOMEM : CSM_ECUDA;
+        }
+    }
+    cudaError_t e = cudaMemcpy(g->w_block, host.data(), host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    return CSM_OK;
 }
 
 static bool valid_dtype(csm_dtype t) { return t == CSM_F32 || t == CSM_F64 || t == CSM_BF16 || t == CSM_F16; }

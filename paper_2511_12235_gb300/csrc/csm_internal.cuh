@@ -60,6 +60,7 @@ struct csm_geom_s {
     int nu = 0, nv = 1;
     double du = 1, dv = 1, u_off = 0, v_off = 0;
     int device = 0;
+    void* w_block = nullptr;       // per-element sensitivity weights (float then double), or none
     void* d_block = nullptr;
     size_t d_bytes = 0;
     csm::DeviceTables t;
@@ -94,9 +95,21 @@ struct Geo {
     const float4* rowq4;
     const long long* colt_fx;
     const double* colt_d;
+    // per-element sensitivity weights w[v][l][k] (NULL: all 1), float and double copies
+    const float* ew_f;
+    const double* ew_d;
 };
 
 Geo make_geo(const csm_geom_s* g);
+
+// Sensitivity weight of element i = (v nv + l) nu + k (1 without weights).
+template <typename T> __device__ __forceinline__ T elem_weight(const Geo& g, size_t i);
+template <> __device__ __forceinline__ float elem_weight<float>(const Geo& g, size_t i) {
+    return g.ew_f ? g.ew_f[i] : 1.0f;
+}
+template <> __device__ __forceinline__ double elem_weight<double>(const Geo& g, size_t i) {
+    return g.ew_d ? g.ew_d[i] : 1.0;
+}
 
 // Most detector row corners (rows + 1) that one voxel's footprint can span in one view; the
 // 3D kernels keep one value per corner in registers.  Geometries beyond it are refused.

@@ -99,17 +99,19 @@ __global__ void __launch_bounds__(256) prep_image_2d(const void* __restrict__ x,
 }
 
 // p[b][v][k] -> ps[((v * Q + q) * nu + k) * VW + r]
+// (the element's sensitivity weight applied: the back projection of diag(w) p)
 template <typename T, int NB>
-__global__ void prep_sino_2d(const void* __restrict__ p, int pdt, int B, int b_off, int V, int nu,
+__global__ void prep_sino_2d(Geo g, const void* __restrict__ p, int pdt, int B, int b_off, int V, int nu,
                              T* __restrict__ ps) {
     constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)V * nu) return;
     const size_t v = i / nu, k = i % nu;
+    const T w = elem_weight<T>(g, i);
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb) {
         const int b = b_off + bb;
-        ps[((v * Q + bb / VW) * nu + k) * VW + bb % VW] = b < B ? load_any<T>(p, (size_t)b * V * nu + i, pdt) : T(0);
+        ps[((v * Q + bb / VW) * nu + k) * VW + bb % VW] = b < B ? w * load_any<T>(p, (size_t)b * V * nu + i, pdt) : T(0);
     }
 }
 
@@ -222,8 +224,10 @@ __global__ void __launch_bounds__(64) fwd2d_ray(Geo g, const T* __restrict__ xs0
     for (int i = 0; i < NB; ++i) {
         const int b = b_off + i;
         if (b < B) {
-            store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k, pdt, acc[i] * scale, accumulate != 0);
-            if (two) store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k + 1, pdt, acc2[i] * scale, accumulate != 0);
+            store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k, pdt,
+                         acc[i] * scale * elem_weight<T>(g, (size_t)v * g.nu + k), accumulate != 0);
+            if (two) store_any<T>(p, ((size_t)b * g.n_views + v) * g.nu + k + 1, pdt,
+                                  acc2[i] * scale * elem_weight<T>(g, (size_t)v * g.nu + k + 1), accumulate != 0);
         }
     }
 }
@@ -418,21 +422,22 @@ __global__ void __launch_bounds__(256) export2d_kernel(Geo g, ExportArgs ea) {
             prev = cur;
             if (!(fabs(wt) > thr)) continue;
             const long long row_e = (long long)v * g.nu + k;
+            const T ew = elem_weight<T>(g, (size_t)row_e);
             switch (ea.mode) {
                 case 0: ++n; break;
                 case 1: {
                     const long long slot = ea.row_ptr[pix] + n++;
                     ea.col[slot] = (int)row_e;
-                    if (ea.dbl) ((double*)ea.val)[slot] = (double)(wt * scale);
-                    else ((float*)ea.val)[slot] = (float)(wt * scale);
+                    if (ea.dbl) ((double*)ea.val)[slot] = (double)(wt * scale * ew);
+                    else ((float*)ea.val)[slot] = (float)(wt * scale * ew);
                     break;
                 }
                 case 2: atomicAdd(ea.counts + row_e, 1ull); break;
                 default: {
                     const long long slot = ea.row_ptr[row_e] + atomicAdd(ea.cursor + row_e, 1);
                     ea.col[slot] = (int)pix;
-                    if (ea.dbl) ((double*)ea.val)[slot] = (double)(wt * scale);
-                    else ((float*)ea.val)[slot] = (float)(wt * scale);
+                    if (ea.dbl) ((double*)ea.val)[slot] = (double)(wt * scale * ew);
+                    else ((float*)ea.val)[slot] = (float)(wt * scale * ew);
                     break;
                 }
             }
@@ -486,7 +491,7 @@ static csm_status run_back(const csm_geom_s* gh, const void* p, void* x, int64_t
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1) : T(gh->a * gh->b);
     const size_t n = (size_t)gh->n_views * gh->nu;
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
-        prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(p, (int)pdt, (int)batch, (int)b0,
+        prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0,
                                                                          gh->n_views, gh->nu, ps);
         dim3 bb(BTX, BTY, BG), bg((gh->nx + BTX - 1) / BTX, (gh->ny + BTY - 1) / BTY);
         back2d_vox<T, NB><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,

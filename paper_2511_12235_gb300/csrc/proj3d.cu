@@ -205,8 +205,8 @@ __global__ void __launch_bounds__(256) prep_vol_3d(const void* __restrict__ x, i
 // stored as q[v][i][r][component][NB] (the sums by parts of the voxel_back_fast form).  Each
 // block differences a 32 x 32 tile of p held in shared memory with a one-element halo.
 template <typename T, int NB>
-__global__ void __launch_bounds__(256) prep_diff_3d(const void* __restrict__ p, int pdt, int B, int b_off, int nu,
-                                                    int nv, T* __restrict__ q) {
+__global__ void __launch_bounds__(256) prep_diff_3d(Geo g, const void* __restrict__ p, int pdt, int B, int b_off,
+                                                    int nu, int nv, T* __restrict__ q) {
     __shared__ T tile[34][34];   // p(i0 - 1 + a, r0 - 1 + b) at tile[b][a], a, b in [0, 33]
     const int i0 = blockIdx.x * 32, r0 = blockIdx.y * 32, v = blockIdx.z;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(256) prep_diff_3d(const void* __restrict__ p, 
             const int k = i0 - 1 + ta, l = r0 - 1 + tb;
             T val = T(0);
             if (k >= 0 && k < nu && l >= 0 && l < nv && b < B)
-                val = load_any3<T>(p, (size_t)b * nvw + (size_t)v * plane + (size_t)l * nu + k, pdt);
+                val = elem_weight<T>(g, (size_t)v * plane + (size_t)l * nu + k) *
+                      load_any3<T>(p, (size_t)b * nvw + (size_t)v * plane + (size_t)l * nu + k, pdt);
             tile[tb][ta] = val;
         }
         __syncthreads();
@@ -1154,7 +1155,9 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             const int bidx = b_off + i;
             if (bidx < B)
                 store_any3<T>(p, (((size_t)bidx * g.n_views + v) * g.nv + L0 + j) * g.nu + kg + kk, pdt,
-                              rows[(kk * rw + j) * NB + i] * scale, accumulate != 0);
+                              rows[(kk * rw + j) * NB + i] * scale *
+                                  elem_weight<T>(g, ((size_t)v * g.nv + L0 + j) * g.nu + kg + kk),
+                              accumulate != 0);
         }
     }
 }
@@ -1221,6 +1224,7 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
 // ---------------------------------------------------------------------------------------
 template <typename T>
 struct ExportSink {
+    const Geo* g;
     ExportArgs a;
     T thr, scale;
     long long vox;     // this voxel's index (column of W)
@@ -1230,21 +1234,22 @@ struct ExportSink {
     __device__ __forceinline__ void add(int k, int l, T wt) {
         if (!(fabs(wt) > thr)) return;
         const long long row_e = (long long)base + (long long)l * nu + k;
+        const T v = wt * scale * elem_weight<T>(*g, (size_t)row_e);
         switch (a.mode) {
             case 0: ++n; break;
             case 1: {
                 const long long slot = a.row_ptr[vox] + n++;
                 a.col[slot] = (int)row_e;
-                if (a.dbl) ((double*)a.val)[slot] = (double)(wt * scale);
-                else ((float*)a.val)[slot] = (float)(wt * scale);
+                if (a.dbl) ((double*)a.val)[slot] = (double)v;
+                else ((float*)a.val)[slot] = (float)v;
                 break;
             }
             case 2: atomicAdd(a.counts + row_e, 1ull); break;
             default: {
                 const long long slot = a.row_ptr[row_e] + atomicAdd(a.cursor + row_e, 1);
                 a.col[slot] = (int)vox;
-                if (a.dbl) ((double*)a.val)[slot] = (double)(wt * scale);
-                else ((float*)a.val)[slot] = (float)(wt * scale);
+                if (a.dbl) ((double*)a.val)[slot] = (double)v;
+                else ((float*)a.val)[slot] = (float)v;
                 break;
             }
         }
@@ -1266,6 +1271,7 @@ __global__ void __launch_bounds__(32 * BW) export3d_kernel(Geo g, ExportArgs ea)
     int* pos = pos_s[wid];
     for (int i = lane; i < ZWN; i += 32) pos[i] = 0;
     ExportSink<T> sink;
+    sink.g = &g;
     sink.a = ea;
     sink.thr = (T)ea.thr;
     sink.scale = (T)ea.scale;
@@ -1402,7 +1408,7 @@ static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_
     constexpr int kTop = sizeof(T) == 8 ? 128 : 512 / NB;   // largest window instantiated
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 tb(32, 8), tg((gh->nu + 1 + 31) / 32, (gh->nv + 2 + 31) / 32, gh->n_views);
-        prep_diff_3d<T, NB><<<tg, tb, 0, st>>>(p, (int)pdt, (int)batch, (int)b0, gh->nu, gh->nv, ps);
+        prep_diff_3d<T, NB><<<tg, tb, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0, gh->nu, gh->nv, ps);
         csm_status r;
         if (zw >= kTop) r = launch_back3<T, NB, kTop>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
         else if (zw >= 256) r = launch_back3<T, NB, (kTop >= 256 ? 256 : 64)>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);

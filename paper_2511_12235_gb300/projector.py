@@ -154,6 +154,15 @@ class Projector:
                           ws.data_ptr(), ws.numel(), stream)
         return out[0] if single else out
 
+    def set_element_weights(self, weights) -> None:
+        """Per-element detector sensitivity weights (array of sino_shape, or None for all 1):
+        forward returns w * (W x), back projects w * p."""
+        if weights is None:
+            capi.csm_geom_set_element_weights(self.handle, None)
+            return
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64).reshape(self.sino_shape))
+        capi.csm_geom_set_element_weights(self.handle, w.ctypes.data)
+
     def forward_line(self, x: torch.Tensor, model: str = "siddon", lines: int = 1,
                      out: torch.Tensor | None = None) -> torch.Tensor:
         """p = W_line x for a line-based comparator model ("siddon" or "joseph"), the mean over
