@@ -58,8 +58,10 @@ typedef enum { CSM_F32 = 0, CSM_F64 = 1, CSM_BF16 = 2, CSM_F16 = 3 } csm_dtype;
 #define CSM_ACCUMULATE        1   /* add into the output instead of overwriting it           */
 #define CSM_RELATIVE_WEIGHTS  2   /* entries divided by the voxel measure ab (abc), as in the
                                      paper's A_3, A_4, Vol_rel                                */
-#define CSM_VOXEL_DRIVEN      4   /* forward only: the voxel-driven scatter variant; not built
-                                     (CSM_EUNSUPPORTED): the ray-driven gather is the forward */
+#define CSM_VOXEL_DRIVEN      4   /* forward only: the voxel-driven scatter variant (the form of
+                                     the paper's Algorithm 1): shared-memory partial sums of
+                                     detector elements per CTA, then global atomics; FP sums in
+                                     no fixed order; workspace from csm_workspace_bytes(op = 2) */
 #define CSM_EXPORT_TRANSPOSE  8   /* csm_export_csr: rows are voxels (the CSR of W^T)         */
 
 /* 2D fan-beam geometry.  angles == NULL means phi_v = 2 pi v / n_views. */
@@ -117,8 +119,9 @@ void csm_geom_free(csm_geom_t geom);
 csm_status csm_geom_set_element_weights(csm_geom_t geom, const double* weights);
 
 /* Bytes of caller-provided device workspace that csm_forward / csm_back need for this
- * geometry, batch and arithmetic type (op: 0 = forward, 1 = back).  The workspace holds
- * the batch-interleaved copies of the input that the kernels gather from. */
+ * geometry, batch and arithmetic type (op: 0 = forward, 1 = back, 2 = forward with
+ * CSM_VOXEL_DRIVEN).  The workspace holds the batch-interleaved copies of the input that the
+ * kernels gather from (and the voxel-driven forward's sums). */
 csm_status csm_workspace_bytes(csm_geom_t geom, int op, int64_t batch, csm_dtype compute,
                                size_t* bytes);
 

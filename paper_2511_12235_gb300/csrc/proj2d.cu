@@ -29,6 +29,7 @@ size_t workspace_2d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
     const size_t es = dbl ? 8 : 4;
     const size_t nb = chunk_for(batch);
     if (op == 0) return 2 * al256((size_t)g->nx * g->ny * nb * es);
+    if (op == 2) return al256((size_t)g->n_views * g->nu * es);   // voxel-driven forward: sums of one item
     return al256((size_t)g->n_views * g->nu * nb * es);
 }
 
@@ -360,6 +361,102 @@ __global__ void __launch_bounds__(BTX * BTY * BG) back2d_vox(Geo g, const T* __r
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Forward projection, voxel-driven (the scatter form of the paper's Algorithm 1): a block of
+// 16 x 16 pixels takes a set of views; per view its pixels add their entries W x into
+// shared-memory partial sums of the elements the block reaches (found by a block-wide
+// min / max of the pixels' element ranges), then every nonzero partial is added to the
+// sinogram sums in global memory with one atomic.  The order of the FP additions is not
+// fixed.
+// ---------------------------------------------------------------------------------------
+constexpr int kPE = 256;      // partial elements per block and view
+constexpr int kVPB = 8;       // views per block
+
+template <typename T>
+__global__ void __launch_bounds__(256) fwd2d_vox(Geo g, const void* __restrict__ x, int xdt, int b,
+                                                 T* __restrict__ pacc) {
+    __shared__ T part[kPE];
+    __shared__ int kr[2];
+    const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
+    const int tid = threadIdx.y * 16 + threadIdx.x;
+    const bool inside = ix < g.nx && iy < g.ny;
+    const T xv = inside ? load_any<T>(x, ((size_t)b * g.ny + iy) * g.nx + ix, xdt) : T(0);
+    const T X0 = GeoT<T>::x0(g) + ix * GeoT<T>::a(g), X1 = X0 + GeoT<T>::a(g);
+    const T Y0 = GeoT<T>::y0(g) + iy * GeoT<T>::b(g), Y1 = Y0 + GeoT<T>::b(g);
+    using L = typename LineOf<T>::type;
+    for (int i = tid; i < kPE; i += 256) part[i] = T(0);
+    const int v_end = min((int)(blockIdx.z + 1) * kVPB, g.n_views);
+    for (int v = blockIdx.z * kVPB; v < v_end; ++v) {
+        int k0 = 0, k1 = -1;
+        const bool has = inside && xv != T(0) && pixel_elements<T>(g, v, X0, X1, Y0, Y1, k0, k1);
+        if (tid == 0) { kr[0] = 0x7fffffff; kr[1] = -1; }
+        __syncthreads();
+        if (has) { atomicMin(kr, k0); atomicMax(kr + 1, k1); }
+        __syncthreads();
+        const int kb = kr[0], ke = kr[1];
+        if (ke >= kb) {                                   // block-uniform
+            if (has) {
+                const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
+                const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
+                L l;
+                l.load(g, v, k0, w);
+                T y0, y1;
+                l.offsets(c, y0, y1);
+                T prev = cell_atom(y0, y1, inv_of<T>(g, v, k0));
+                for (int k = k0; k <= k1; ++k) {
+                    l.load(g, v, k + 1, w);
+                    l.offsets(c, y0, y1);
+                    const T cur = cell_atom(y0, y1, inv_of<T>(g, v, k + 1));
+                    const T wt = sigma > 0 ? cur - prev : prev - cur;
+                    prev = cur;
+                    if (wt != T(0)) {
+                        if (k - kb < kPE) atomicAdd(part + (k - kb), wt * xv);
+                        else atomicAdd(pacc + (size_t)v * g.nu + k, wt * xv);
+                    }
+                }
+            }
+            __syncthreads();
+            const int span = min(ke - kb + 1, kPE);
+            for (int i = tid; i < span; i += 256) {
+                const T val = part[i];
+                if (val != T(0)) {
+                    atomicAdd(pacc + (size_t)v * g.nu + kb + i, val);
+                    part[i] = T(0);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// p = scale * w * sums (+ p with CSM_ACCUMULATE), in p's storage type.
+template <typename T>
+__global__ void finish_scatter_2d(Geo g, const T* __restrict__ pacc, void* __restrict__ p, int pdt, int b, T scale,
+                                  int accumulate) {
+    const size_t n = (size_t)g.n_views * g.nu;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        store_any<T>(p, (size_t)b * n + i, pdt, pacc[i] * scale * elem_weight<T>(g, i), accumulate != 0);
+}
+
+template <typename T>
+static csm_status run_forward_vox(const csm_geom_s* gh, const void* x, void* p, int64_t batch, csm_dtype xdt,
+                                  csm_dtype pdt, int flags, void* ws, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    T* pacc = (T*)ws;
+    const size_t n = (size_t)gh->n_views * gh->nu;
+    const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1) : T(gh->a * gh->b);
+    dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16, (gh->n_views + kVPB - 1) / kVPB);
+    for (int64_t b = 0; b < batch; ++b) {
+        cudaError_t e = cudaMemsetAsync(pacc, 0, n * sizeof(T), st);
+        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+        fwd2d_vox<T><<<bg, bb, 0, st>>>(g, x, (int)xdt, (int)b, pacc);
+        finish_scatter_2d<T><<<1216, 256, 0, st>>>(g, pacc, p, (int)pdt, (int)b, scale, (flags & CSM_ACCUMULATE) ? 1 : 0);
+        csm_status s = check_launch();
+        if (s != CSM_OK) return s;
+    }
+    return CSM_OK;
+}
+
 // Number of (pixel, view, element) whose area exceeds 1e-6 of the pixel's.
 __global__ void __launch_bounds__(256) nnz2d_kernel(Geo g, unsigned long long* counter) {
     const int ix = blockIdx.x * 16 + threadIdx.x, iy = blockIdx.y * 16 + threadIdx.y;
@@ -529,7 +626,12 @@ static csm_status back_nb(const csm_geom_s* g, const void* p, void* x, int64_t b
 csm_status forward_2d(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt, csm_dtype pdt,
                       int flags, void* ws, size_t ws_bytes, cudaStream_t st) {
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
-    if (flags & CSM_VOXEL_DRIVEN) return CSM_EUNSUPPORTED;
+    if (flags & CSM_VOXEL_DRIVEN) {
+        if (!ws || ws_bytes < workspace_2d(g, 2, batch, dbl)) return CSM_EINVAL;
+        if ((g->n_views + kVPB - 1) / kVPB > 65535) return CSM_EUNSUPPORTED;
+        return dbl ? run_forward_vox<double>(g, x, p, batch, xdt, pdt, flags, ws, st)
+                   : run_forward_vox<float>(g, x, p, batch, xdt, pdt, flags, ws, st);
+    }
     if (!ws || ws_bytes < workspace_2d(g, 0, batch, dbl)) return CSM_EINVAL;
     if ((g->n_views + 3) / 4 > 65535) return CSM_EUNSUPPORTED;
     return dbl ? fwd_nb<double>(g, x, p, batch, xdt, pdt, flags, ws, st)

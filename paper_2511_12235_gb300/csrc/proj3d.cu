@@ -44,6 +44,10 @@ size_t workspace_3d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
     // back: the differenced sinogram, 4 values per (view, corner 0..nu, plane slot 0..nv+1)
     const size_t sino = al256((size_t)g->n_views * (g->nu + 1) * (g->nv + 2) * 4 * nb * es);
     if (op == 0) return 2 * vol;   // the volume in both walk layouts
+    if (op == 2) {                 // voxel-driven forward: one item's layouts and its sinogram sums
+        const size_t vol1 = al256((size_t)g->nx * g->ny * g->nz * es);
+        return 2 * vol1 + al256((size_t)g->n_views * g->nv * g->nu * es);
+    }
     return sino;
 }
 
@@ -1218,6 +1222,152 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
 }
 
 // ---------------------------------------------------------------------------------------
+// Forward projection, voxel-driven (the scatter form of the paper's Algorithm 1): warps over
+// voxel columns as in the back projection; each warp adds its voxels' entries W x into
+// shared-memory partial sums of the detector rows its chunk of voxels reaches (one per
+// footprint column and row), then adds every nonzero partial to the sinogram sums in global
+// memory with one atomic.  Entries beyond the partials' row range go to global memory
+// directly.  The order of the FP additions is not fixed.
+// ---------------------------------------------------------------------------------------
+constexpr int kPR = 128;   // partial rows per footprint column
+
+template <typename T>
+struct PartialSink {
+    T* part;            // [kMaxG + 1][kPR]
+    T* pacc;            // this view's sums, [nv][nu]
+    int lbase, kfirst, nu;
+    T xv;
+    __device__ __forceinline__ void add(int k, int l, T wt) {
+        const int j = k - kfirst, r = l - lbase;
+        if (j >= 0 && j <= kMaxG && r >= 0 && r < kPR) atomicAdd(part + j * kPR + r, wt * xv);
+        else atomicAdd(pacc + (size_t)l * nu + k, wt * xv);
+    }
+};
+
+template <typename T, int ZW>
+__global__ void __launch_bounds__(32 * BW) fwd3d_vox(Geo g, const T* __restrict__ xs0, T* __restrict__ pacc) {
+    __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
+    __shared__ T ks_s[BW][32 * kKs];
+    __shared__ T part_s[BW][(kMaxG + 1) * kPR];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int col = blockIdx.x * BW + wid;
+    if (col >= g.nx * g.ny) return;
+    const int ix = col % g.nx, iy = col / g.nx;
+    const int zb = blockIdx.y * ZW, ze = min(zb + ZW, g.nz);
+    AtomP<T>* atoms = atoms_s[wid];
+    T* ks = ks_s[wid];
+    T* part = part_s[wid];
+    for (int i = lane; i < (kMaxG + 1) * kPR; i += 32) part[i] = T(0);
+    const T* xcol = xs0 + ((size_t)ix * g.ny + iy) * g.nz;
+    const T c = G3<T>::c(g);
+    for (int v = 0; v < g.n_views; ++v) {
+        ColumnView<T> cv;
+        column_view<T>(g, v, ix, iy, lane, cv);
+        if (!cv.ok) continue;
+        int z0, z1;
+        cone_z_range<T>(g, cv.tmin_w, cv.tmax_w, z0, z1);
+        z0 = max(z0, zb);
+        z1 = min(z1, ze - 1);
+        if (z0 > z1) continue;
+        // skip columns whose voxels in reach are all zero
+        bool nzv = false;
+        for (int zc = z0; zc <= z1 && !__any_sync(0xffffffffu, nzv); zc += 32)
+            if (zc + lane <= z1) nzv = __ldg(xcol + zc + lane) != T(0);
+        if (!__any_sync(0xffffffffu, nzv)) continue;
+        __syncwarp();
+        column_atoms<T>(g, v, ix, iy, cv, lane, atoms);
+        __syncwarp();
+        PartialSink<T> sink;
+        sink.part = part;
+        sink.pacc = pacc + (size_t)v * g.nv * g.nu;
+        sink.kfirst = cv.k_first;
+        sink.nu = g.nu;
+        const int step = cv.fast ? 31 : 32;
+        for (int zc = z0; zc <= z1; zc += step) {
+            const int iz = zc + lane;
+            const bool mine = lane < step && iz <= z1;
+            const T xv = mine ? __ldg(xcol + iz) : T(0);
+            // rows the chunk reaches start at the lowest voxel's first row
+            int l0 = g.nv, l1 = -1;
+            if (mine && xv != T(0)) {
+                const T z0w = G3<T>::z0(g) + iz * c;
+                if (!voxel_rows<T>(g, z0w, z0w + c, cv.tmin_w, cv.tmax_w, l0, l1)) { l0 = g.nv; l1 = -1; }
+            }
+            const int lbase = __reduce_min_sync(0xffffffffu, (unsigned)(l0 + 1)) - 1;
+            const int ltop = (int)__reduce_max_sync(0xffffffffu, (unsigned)(l1 + 1)) - 1;
+            sink.lbase = lbase;
+            sink.xv = xv;
+            if (cv.fast) {
+                int ra = 0;
+                const bool need = mine && xv != T(0);
+                const bool below = __shfl_up_sync(0xffffffffu, need, 1);
+                const int rb = ((need || (lane > 0 && below)) && iz <= z1 + 1)
+                                   ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                __syncwarp();
+                const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
+                if (need)
+                    voxel_entries_fast<T>(g, ix, iy, iz, cv, atoms, atoms[kMaxG], rb, ks + lane * kKs, rt,
+                                          ks + (lane + 1) * kKs, sink);
+            } else if (mine && xv != T(0)) {
+                voxel_entries<T>(g, v, ix, iy, iz, cv, atoms, atoms[kMaxG], sink);
+            }
+            __syncwarp();
+            // flush the partials of the rows reached (elements on the detector only)
+            if (ltop >= lbase) {
+                const int span = min(ltop - lbase + 1, kPR);
+                for (int j = 0; j <= cv.ng; ++j) {
+                    const int k = cv.k_first + j;
+                    for (int r = lane; r < span; r += 32) {
+                        const T val = part[j * kPR + r];
+                        if (val != T(0)) {
+                            if (k >= 0 && k < g.nu) atomicAdd(sink.pacc + (size_t)(lbase + r) * g.nu + k, val);
+                            part[j * kPR + r] = T(0);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// p = scale * w * sums (+ p with CSM_ACCUMULATE), in p's storage type.
+template <typename T>
+__global__ void finish_scatter_3d(Geo g, const T* __restrict__ pacc, void* __restrict__ p, int pdt, int b, T scale,
+                                  int accumulate) {
+    const size_t n = (size_t)g.n_views * g.nv * g.nu;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        store_any3<T>(p, (size_t)b * n + i, pdt, pacc[i] * scale * elem_weight<T>(g, i), accumulate != 0);
+}
+
+template <typename T>
+static csm_status run_fwd3_vox(const csm_geom_s* gh, const void* x, void* p, int64_t batch, csm_dtype xdt,
+                               csm_dtype pdt, int flags, void* ws, cudaStream_t st) {
+    const Geo g = make_geo(gh);
+    const size_t nvox = (size_t)gh->nx * gh->ny * gh->nz;
+    const size_t vol1 = al256(nvox * sizeof(T));
+    T* xs0 = (T*)ws;
+    T* xs1 = (T*)((char*)ws + vol1);
+    T* pacc = (T*)((char*)ws + 2 * vol1);
+    const size_t nsino = (size_t)gh->n_views * gh->nv * gh->nu;
+    const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
+    const size_t ncol = (size_t)gh->nx * gh->ny;
+    constexpr int ZW = 64;
+    for (int64_t b = 0; b < batch; ++b) {
+        dim3 tb(32, 8), tg((gh->nx + 31) / 32, (gh->nz + 31) / 32, gh->ny);
+        prep_vol_3d<T, 1><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b, gh->nx, gh->ny, gh->nz, xs0, xs1);
+        cudaError_t e = cudaMemsetAsync(pacc, 0, nsino * sizeof(T), st);
+        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+        dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZW - 1) / ZW);
+        fwd3d_vox<T, ZW><<<bg, bb, 0, st>>>(g, xs0, pacc);
+        finish_scatter_3d<T><<<1216, 256, 0, st>>>(g, pacc, p, (int)pdt, (int)b, scale, (flags & CSM_ACCUMULATE) ? 1 : 0);
+        csm_status s = check_launch();
+        if (s != CSM_OK) return s;
+    }
+    return CSM_OK;
+}
+
+// ---------------------------------------------------------------------------------------
 // Sparse export: the same per-voxel entries (column-warps, 64-voxel windows as the count),
 // written as rows of W^T (voxels; per-voxel counts and write positions kept in shared memory,
 // so the entries of a row come in view, row, column order) or of W (elements; atomics).
@@ -1422,10 +1572,14 @@ static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_
 csm_status forward_3d(const csm_geom_s* g, const void* x, void* p, int64_t batch, csm_dtype xdt, csm_dtype pdt,
                       int flags, void* ws, size_t ws_bytes, cudaStream_t st) {
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
-    if (flags & CSM_VOXEL_DRIVEN) return CSM_EUNSUPPORTED;
-    if (!ws || ws_bytes < workspace_3d(g, 0, batch, dbl)) return CSM_EINVAL;
     if (g->n_views > 65535 || (g->nv + 31) / 32 > 65535 || g->ny > 65535 || (g->nz + 31) / 32 > 65535)
         return CSM_EUNSUPPORTED;
+    if (flags & CSM_VOXEL_DRIVEN) {
+        if (!ws || ws_bytes < workspace_3d(g, 2, batch, dbl)) return CSM_EINVAL;
+        return dbl ? run_fwd3_vox<double>(g, x, p, batch, xdt, pdt, flags, ws, st)
+                   : run_fwd3_vox<float>(g, x, p, batch, xdt, pdt, flags, ws, st);
+    }
+    if (!ws || ws_bytes < workspace_3d(g, 0, batch, dbl)) return CSM_EINVAL;
     switch (chunk3(batch)) {
         case 4: return dbl ? run_fwd3<double, 4>(g, x, p, batch, xdt, pdt, flags, ws, st)
                            : run_fwd3<float, 4>(g, x, p, batch, xdt, pdt, flags, ws, st);

@@ -104,8 +104,8 @@ class Projector:
                 out_dtype: torch.dtype | None = None, variant: str | None = None) -> torch.Tensor:
         """p = W x.  x: [B, *vol_shape] or vol_shape on this device.
 
-        variant: "ray" (ray-driven gather; the only one built: the voxel-driven scatter
-        form is refused with CSM_EUNSUPPORTED)."""
+        variant: "ray" (ray-driven gather, the default) or "voxel" (voxel-driven scatter with
+        shared-memory partial sums and atomics, the form of the paper's Algorithm 1)."""
         if variant is None:
             variant = "ray"
         if variant == "voxel":
@@ -125,7 +125,7 @@ class Projector:
             out = out.view((B,) + tuple(self.sino_shape))
             assert out.is_contiguous() and out.device == self.device
         compute = torch.float64 if torch.float64 in (xb.dtype, out.dtype) else torch.float32
-        ws = self.workspace(0, B, compute)
+        ws = self.workspace(2 if flags & capi.CSM_VOXEL_DRIVEN else 0, B, compute)
         stream = torch.cuda.current_stream(self.device).cuda_stream
         with nvtx_range("csm_forward"):
             capi.csm_forward(self.handle, xb.data_ptr(), out.data_ptr(), B, _dt(xb.dtype), _dt(out.dtype), flags,
