@@ -131,16 +131,20 @@ csm_status csm_workspace_bytes(csm_geom_t geom, int op, int64_t batch, csm_dtype
  *   Arithmetic is FP64 when x_dt or p_dt is CSM_F64, else FP32 (BF16/F16 are storage
  *   types only).  workspace: device pointer of at least csm_workspace_bytes(op = 0);
  *   may alias neither x nor p.  Returns CSM_EINVAL when the workspace is too small.
- *   Ray-driven gather: each element of p is written once.  2D sums in a fixed order
- *   (bit-reproducible); the 3D forward adds a row's entries through shared-memory atomics
- *   of one warp, so its FP32 sums may differ in the last bits between runs. */
+ *   Ray-driven gather: each element of p is written once, summed in a fixed order
+ *   (bit-reproducible) -- in 3D wherever neighbouring row planes lie farther apart than twice
+ *   a plane's height change across a voxel (as in the 128^3 and 512^3 cone-beam geometries);
+ *   elsewhere the 3D forward adds a row's entries through shared-memory atomics of one warp
+ *   and its FP32 sums may differ in the last bits between runs.  With CSM_VOXEL_DRIVEN: the
+ *   scatter variant. */
 csm_status csm_forward(csm_geom_t geom, const void* x, void* p, int64_t batch,
                        csm_dtype x_dt, csm_dtype p_dt, int flags,
                        void* workspace, size_t workspace_bytes, void* cuda_stream);
 
 /* x = W^T p, the adjoint of csm_forward with the same entries (Section "Algorithm 1" and
  * the paper's adjoint-mismatch check, Section "Numerical Experiments").  Gather form (one
- * thread per pixel in 2D, one lane per voxel in 3D), fixed summation order, no atomics.
+ * thread per pixel in 2D, one lane per voxel in 3D, where the voxel's value is summed by
+ * parts over a differenced sinogram), fixed summation order, no atomics.
  * Arguments as for csm_forward with the roles of x and p exchanged (workspace from
  * csm_workspace_bytes(op = 1)). */
 csm_status csm_back(csm_geom_t geom, const void* p, void* x, int64_t batch,
