@@ -932,13 +932,14 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
 template <typename T, int NB>
 __device__ __forceinline__ void cell_forward_fast(const Geo& g, const ColumnView<T>& cv, const AtomP<T>* atoms,
                                                   const AtomP<T>& full, const T* __restrict__ xcol, int lane, int kg,
-                                                  int nk, int L0, int nrow, int rw, T* rows) {
+                                                  int nk, int L0, int nrow, int rw, T* rows, int zlo, int zhi) {
     const T c = G3<T>::c(g);
     const int ng = cv.ng, na = ng + 1;
-    // planes that can reach into the grid: around the heights -1 and nz + 1 (m < 1/2)
+    // planes that can reach the nonzero voxels zlo .. zhi: around the heights zlo - 1 and zhi + 2
+    // (m < 1/2); rows between two planes both below or both above them add exactly nothing
     const T tc = cv.dh + cv.dl;
-    const T ra_f = (G3<T>::div(T(-1) - T(0.5) * T(g.nz), tc) * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
-    const T rb_f = (G3<T>::div(T(g.nz + 1) - T(0.5) * T(g.nz), tc) * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
+    const T ra_f = (G3<T>::div(T(zlo - 1) - T(0.5) * T(g.nz), tc) * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
+    const T rb_f = (G3<T>::div(T(zhi + 2) - T(0.5) * T(g.nz), tc) * G3<T>::sdd(g) - G3<T>::v0(g)) * G3<T>::idv(g);
     const int plast = L0 + nrow;                      // planes L0 .. L0 + nrow bound the window's rows
     int r_first = L0, r_last = plast;
     {
@@ -958,8 +959,9 @@ __device__ __forceinline__ void cell_forward_fast(const Geo& g, const ColumnView
         int izr = 0;
         if (r <= r_last) {
             T q, iq;
-            const T H = plane_height(g, r, 0, cv.dh, cv.dl, q, iq);   // height above the grid's bottom
-            izr = (int)floor(H);
+            // the voxel holding the plane's centre: a rough height above the grid's bottom (off by
+            // at most one voxel near a face), then the exact height relative to that voxel
+            izr = (int)floor(G3<T>::q(g, r) * (cv.dh + cv.dl) + T(0.5) * T(g.nz));
             T h = plane_height(g, r, izr, cv.dh, cv.dl, q, iq);       // the same, relative to voxel izr
             if (h < T(0)) { izr -= 1; h += T(1); }
             else if (h >= T(1)) { izr += 1; h -= T(1); }
@@ -1109,17 +1111,23 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
             const T* xcol = xs + ((size_t)w * nc + cc) * g.nz * NB;
-            // cells whose voxels in reach are all zero add nothing: skip them before any table
-            // is built
-            bool nzv = false;
-            for (int zb = izlo; zb <= izhi && !__any_sync(0xffffffffu, nzv); zb += 32) {
+            // the voxels in reach that are nonzero: cells with none add nothing and are skipped
+            // before any table is built; planes below or above all of them add nothing either
+            int znz_lo = 0x7fffffff, znz_hi = -1;
+            for (int zb = izlo; zb <= izhi; zb += 32) {
                 const int iz = zb + lane;
+                bool nzv = false;
                 if (iz <= izhi) {
 #pragma unroll
                     for (int i = 0; i < NB; ++i) nzv |= __ldg(xcol + (size_t)iz * NB + i) != T(0);
                 }
+                const unsigned mz = __ballot_sync(0xffffffffu, nzv);
+                if (mz) {
+                    if (znz_lo == 0x7fffffff) znz_lo = zb + __ffs(mz) - 1;
+                    znz_hi = zb + 31 - __clz(mz);
+                }
             }
-            if (!__any_sync(0xffffffffu, nzv)) continue;
+            if (znz_hi < 0) continue;
             __syncwarp();
             for (int it = lane; it < cv.ng * 5; it += 32) {
                 const int i = it / 5;
@@ -1127,7 +1135,8 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             }
             __syncwarp();
             if (cv.fast) {
-                cell_forward_fast<T, NB>(g, cv, atoms, atoms[kMaxG], xcol, lane, kg, nk, L0, nrow, rw, rows);
+                cell_forward_fast<T, NB>(g, cv, atoms, atoms[kMaxG], xcol, lane, kg, nk, L0, nrow, rw, rows, znz_lo,
+                                         znz_hi);
                 __syncwarp();
                 continue;
             }
