@@ -650,10 +650,11 @@ __device__ __forceinline__ T kink_tail(const AtomP<T>& P, T gw, T q, T iq, bool 
 // The plane (if any) that meets the bottom face of voxel iz inside the cell, and its K for the
 // whole-cell atom (slot 0) and each crossing line's atom (slots 1 .. ng), written to kslot.
 // Returns the plane's index, or -1; ra receives the first plane whose height at the cell
-// centre is at or above the face (0 .. nv + 1).  Requires cv.fast.
+// centre is at or above the face (0 .. nv + 1), ha and qa its height above the face (units of
+// c) and q when ra <= nv.  Requires cv.fast.
 template <typename T>
 __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
-                                         const AtomP<T>& full, T* kslot, int& ra) {
+                                         const AtomP<T>& full, T* kslot, int& ra, T& ha, T& qa) {
     // nearest planes: q t_c / c = iz - nz/2 at the face, planes q_r = (v0 + r dv) / sdd
     const T fz = T(iz) - T(0.5) * T(g.nz);
     const T qf = G3<T>::div(fz, cv.dh + cv.dl);
@@ -664,13 +665,16 @@ __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<
     int rb = -1;
     T hb = T(0), qb = T(0), iqb = T(0);
     ra = r0 + 1;
+    ha = T(0);
+    qa = T(0);
+    bool found = false;
 #pragma unroll
     for (int c2 = 0; c2 < 2; ++c2) {
         const int r = r0 + c2;
         if (r >= 0 && r <= g.nv) {
             T q, iq;
             const T h = plane_height(g, r, iz, cv.dh, cv.dl, q, iq);
-            if (c2 == 0 && h >= T(0)) ra = r0;
+            if (!found && h >= T(0)) { ra = r; ha = h; qa = q; found = true; }
             if (fabs(h) < fabs(q) * cv.margin_c) { rb = r; hb = h; qb = q; iqb = iq; }
         }
     }
@@ -699,8 +703,8 @@ __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<
 // differenced projections (prep_diff_3d).
 template <typename T, int NB>
 __device__ __forceinline__ void voxel_back_fast(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
-                                                const AtomP<T>& full, const T* __restrict__ qv, int ra, int rtop,
-                                                int rb, const T* kb, int rt, const T* kt, T (&sum)[NB]) {
+                                                const AtomP<T>& full, const T* __restrict__ qv, int ra, T ha, T qa,
+                                                int rtop, int rb, const T* kb, int rt, const T* kt, T (&sum)[NB]) {
     const int ng = cv.ng;
     const int ns = g.nv + 2;
     const T c = G3<T>::c(g);
@@ -715,9 +719,11 @@ __device__ __forceinline__ void voxel_back_fast(const Geo& g, int iz, const Colu
     for (int n = 0; n < NB; ++n) acc[n] = T(0);
     const int rlo = ra < 0 ? 0 : ra, rhi = rtop > g.nv + 1 ? g.nv + 1 : rtop;
 #pragma unroll 1
+    T q = qa, hr = ha;                  // the first plane's height came with ra
     for (int r = rlo; r < rhi; ++r) {   // planes with their centre inside the voxel (r <= nv)
-        T q, iq;
-        const T gw = plane_height(g, r, iz, cv.dh, cv.dl, q, iq) * c;
+        T iq;
+        if (r != rlo) hr = plane_height(g, r, iz, cv.dh, cv.dl, q, iq);
+        const T gw = hr * c;
 #pragma unroll
         for (int j = 0; j < kMaxG; ++j) {
             if (j < ng) {
@@ -831,7 +837,7 @@ constexpr int ZWN = 64;   // voxels of a column per warp in the nnz count
 
 template <typename T, int NB, int ZW>
 __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x, int xdt,
-                                                      int B, int b_off, T scale, int accumulate) {
+                                                      int B, int b_off, T scale, int accumulate, int v_begin, int v_end) {
     __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
     __shared__ T acc_s[BW][NB * ZW];
     __shared__ T ks_s[BW][32 * kKs];
@@ -844,7 +850,7 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
     T* ks = ks_s[wid];
     T* acc = acc_s[wid];                                  // acc[b * ZW + (iz - zb)]
     for (int i = lane; i < NB * ZW; i += 32) acc[i] = T(0);
-    for (int v = 0; v < g.n_views; ++v) {
+    for (int v = v_begin; v < v_end; ++v) {
         ColumnView<T> cv;
         column_view<T>(g, v, ix, iy, lane, cv);
         if (!cv.ok) continue;                              // warp-uniform
@@ -864,13 +870,15 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
             for (int zc = z0; zc <= z1; zc += 31) {
                 const int iz = zc + lane;
                 int ra = 0;
-                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                T ha = T(0), qa = T(0);
+                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra, ha, qa)
+                                            : -1;
                 __syncwarp();
                 const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
                 const int rtop = __shfl_down_sync(0xffffffffu, ra, 1);
                 if (lane < 31 && iz <= z1) {
                     T vs[NB];
-                    voxel_back_fast<T, NB>(g, iz, cv, atoms, atoms[kMaxG], sink.pv, ra, rtop, rb, ks + lane * kKs, rt,
+                    voxel_back_fast<T, NB>(g, iz, cv, atoms, atoms[kMaxG], sink.pv, ra, ha, qa, rtop, rb, ks + lane * kKs, rt,
                                            ks + (lane + 1) * kKs, vs);
 #pragma unroll
                     for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += vs[i];
@@ -1212,7 +1220,8 @@ __global__ void __launch_bounds__(32 * BW) nnz3d_kernel(Geo g, unsigned long lon
             for (int zc = z0; zc <= z1; zc += 31) {
                 const int iz = zc + lane;
                 int ra = 0;
-                const int rb = iz <= z1 + 1 ? face_kink<float>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                float ha_, qa_;   // unused here
+                const int rb = iz <= z1 + 1 ? face_kink<float>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra, ha_, qa_) : -1;
                 __syncwarp();
                 const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
                 if (lane < 31 && iz <= z1)
@@ -1308,10 +1317,11 @@ __global__ void __launch_bounds__(32 * BW) fwd3d_vox(Geo g, const T* __restrict_
             sink.xv = xv;
             if (cv.fast) {
                 int ra = 0;
+                T ha_, qa_;   // unused here
                 const bool need = mine && xv != T(0);
                 const bool below = __shfl_up_sync(0xffffffffu, need, 1);
                 const int rb = ((need || (lane > 0 && below)) && iz <= z1 + 1)
-                                   ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                                   ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra, ha_, qa_) : -1;
                 __syncwarp();
                 const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
                 if (need)
@@ -1452,7 +1462,8 @@ __global__ void __launch_bounds__(32 * BW) export3d_kernel(Geo g, ExportArgs ea)
             for (int zc = z0; zc <= z1; zc += 31) {
                 const int iz = zc + lane;
                 int ra = 0;
-                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra) : -1;
+                T ha_, qa_;   // unused here
+                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra, ha_, qa_) : -1;
                 __syncwarp();
                 const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
                 if (lane < 31 && iz <= z1) {
@@ -1547,14 +1558,33 @@ static int back_window(const csm_geom_s* g, bool dbl, int nb) {
     return 64;
 }
 
+// Views per back-projection launch: every resident warp works on the same few views, so their
+// slices of the differenced sinogram stay in L2 (about 64 MiB of them, one batch item's worth,
+// so that the grouping and the summation order do not depend on the batch) instead of every
+// warp reading its own view from DRAM.  Each group adds its sums to x (read-modify-write, one
+// warp per voxel, a fixed order); outputs in BF16 / F16 are written once, from all views.
+static int back_view_group(const csm_geom_s* g, size_t elem, csm_dtype xdt, bool dbl) {
+    const bool exact_x = dbl ? xdt == CSM_F64 : xdt == CSM_F32;
+    const size_t slice = (size_t)(g->nu + 1) * (g->nv + 2) * 4 * elem;
+    if (!exact_x) return g->n_views;
+    const size_t v = ((size_t)64 << 20) / (slice > 0 ? slice : 1);
+    return (int)std::max<size_t>(1, std::min<size_t>(v, (size_t)g->n_views));
+}
+
 template <typename T, int NB, int ZW>
 static csm_status launch_back3(const Geo& g, const csm_geom_s* gh, const T* ps, void* x, int64_t batch,
                                csm_dtype xdt, int64_t b0, T scale, int flags, cudaStream_t st) {
     const size_t ncol = (size_t)gh->nx * gh->ny;
     dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZW - 1) / ZW);
-    back3d_vox<T, NB, ZW><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
-                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
-    return check_launch();
+    const int vg = back_view_group(gh, sizeof(T), xdt, sizeof(T) == 8);
+    for (int v0 = 0; v0 < gh->n_views; v0 += vg) {
+        const int acc = (v0 > 0 || (flags & CSM_ACCUMULATE)) ? 1 : 0;
+        back3d_vox<T, NB, ZW><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale, acc, v0,
+                                                std::min(v0 + vg, gh->n_views));
+        csm_status s = check_launch();
+        if (s != CSM_OK) return s;
+    }
+    return CSM_OK;
 }
 
 template <typename T, int NB>
