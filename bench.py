@@ -36,11 +36,16 @@ WORKLOADS = {
     "cone3d_128": dict(batch=1, dtype="f32"),
     "cone3d_512": dict(batch=1, dtype="f32"),
 }
-# algorithmic FP32 operations per nonzero entry, plus one multiply-add per batch item:
-#   2D: two cell atoms and their difference (12 flops)
-#   3D: one Phi (two relu integrals over a top-view atom, shared by four entries) and the
-#       double difference (40 flops)
-FLOPS_PER_ENTRY_WEIGHT = {2: 12, 3: 40}
+# Algorithmic FP operations (add / sub / mul 1, FMA 2, divide 1) of the kernels as implemented, per
+# nonzero entry of W, as (geometry part, part per batch item).  2D: two cell atoms and their
+# difference per entry, one multiply-add per item.  3D: counted per event of the fast forms
+# (face corrections, planes inside a voxel, first plane above; plane rows and cells of the
+# forward) and divided by the entries, with the event counts of the 512^3 workload:
+#   back    93 flops per (voxel, view) = 75 + 18 per item, 7.85 entries per (voxel, view)
+#   forward 59 flops per plane row = 33 + 26 per item, 0.10 plane rows per entry on the phantom
+#           (rows outside the column's nonzero voxels are skipped), plus 1390 per cell set-up
+ALG_FLOPS = {(2, "forward"): (12.0, 2.0), (2, "back"): (12.0, 2.0),
+             (3, "back"): (9.6, 2.3), (3, "forward"): (4.35, 2.6)}
 L2_FLUSH_BYTES = 512 << 20
 # the reference arm (the oracle) is sized so that all its steps take about this long
 REFERENCE_TOTAL_S = 120.0
@@ -166,7 +171,7 @@ def kernel_source_hash() -> str:
 
 
 def dram_traffic(workload: str, kernel: str):
-    """DRAM bytes (read + write) per launch of `kernel` ("forward" / "back") on `workload`
+    """DRAM bytes (read + write) per call of `kernel` ("forward" / "back") on `workload`
     from the committed ncu capture (profiles/dram_traffic.json), or None when there is none
     or the kernel sources changed since it was taken."""
     try:
@@ -178,6 +183,27 @@ def dram_traffic(workload: str, kernel: str):
         return None
     v = d.get(workload, {}).get(kernel)
     return float(v) if v is not None else None
+
+
+def count_launches(step):
+    """Kernels of this library launched by one (untimed) step, counted by the CUDA activity
+    profiler: (count, {kernel: launches}), or (None, reason) when the profiler is unavailable.
+    The library's kernels live in the namespace csm."""
+    import torch
+    try:
+        from torch.profiler import ProfilerActivity, profile
+        torch.cuda.synchronize()
+        with profile(activities=[ProfilerActivity.CUDA]) as prof:
+            step()
+            torch.cuda.synchronize()
+        names = {}
+        for ev in prof.events():
+            if getattr(ev, "device_type", None) is not None and "CUDA" in str(ev.device_type) and "csm::" in ev.name:
+                key = ev.name.split("<")[0].replace("void ", "")
+                names[key] = names.get(key, 0) + 1
+        return (sum(names.values()) if names else None), names
+    except Exception as e:  # profiler missing on this build: no claim
+        return None, "not counted: %s" % type(e).__name__
 
 
 def measure_alu_peak(dev, clocks_gpu: int):
@@ -457,6 +483,8 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in es) / n
 
+    launches_per_step, launch_names = count_launches(step)
+
     t_fwd = time_op(lambda: P.forward(x, out=p))
     t_back = time_op(lambda: P.back(p, out=xb))
     p_dense = torch.empty_like(p)
@@ -491,8 +519,8 @@ def run_ours(args, rank, world, local):
 
     # roofline of the dominant kernel (ALU bound: algorithmic flops / launch time)
     dom, t_dom = ("forward", t_fwd) if t_fwd >= t_back else ("back", t_back)
-    fpe = FLOPS_PER_ENTRY_WEIGHT[g["dim"]]
-    flops = nnz * (fpe + 2 * batch)
+    fpe, fpb = ALG_FLOPS[(g["dim"], dom)]
+    flops = nnz * (fpe + fpb * batch)
     achieved = flops / (t_dom / 1e3) / 1e12
     fp64 = tdt == torch.float64
     long_kernel = t_dom > 100.0
@@ -513,7 +541,8 @@ def run_ours(args, rank, world, local):
                    "l2": "flushed before every timed step (512 MiB write, untimed); inputs larger than L2"
                          if g["dim"] == 3 else "flushed before every timed step (512 MiB write, untimed)",
                    "step": "forward over all views + back projection of the batch"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": launches_per_step * args.steps if launches_per_step is not None else None,
+        "gpu_launches_per_step": launch_names,
         "gvoxel_views_per_s": voxel_views,
         "kernels_ms": {"forward": t_fwd, "back": t_back, "forward_dense_input": t_fwd_dense},
         "dense_input": {"value": dense_value, "unit": UNIT, "x_zero_fraction": 0.0,
@@ -521,9 +550,11 @@ def run_ours(args, rank, world, local):
                                 "every entry of W is evaluated and applied) and the timed back projection"},
         "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                      "frac": achieved / pk, "traffic": dram_traffic(wl, dom),
-                     "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
+                     "traffic_unit": "bytes per call of the kernel (ncu dram__bytes_read.sum + dram__bytes_write.sum; "
+                                     "the back projection's launches over its view groups summed, like its time)",
                      "peak_note": "%s rate measured in this run by csm_fma_rate (of measured); algorithmic "
-                                  "flops = nnz x (%d + 2 x batch)" % (which, fpe)},
+                                  "flops = nnz x (%.2f + %.2f x batch), the FP operations of the kernel as "
+                                  "implemented per entry" % (which, fpe, fpb)},
         "alu_peak_measured": peak,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_pin.numel() * x_pin.element_size()),
