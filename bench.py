@@ -196,12 +196,21 @@ def count_launches(step):
         with profile(activities=[ProfilerActivity.CUDA]) as prof:
             step()
             torch.cuda.synchronize()
-        names = {}
+        names, seen = {}, []
         for ev in prof.events():
-            if getattr(ev, "device_type", None) is not None and "CUDA" in str(ev.device_type) and "csm::" in ev.name:
-                key = ev.name.split("<")[0].replace("void ", "")
-                names[key] = names.get(key, 0) + 1
-        return (sum(names.values()) if names else None), names
+            name = ev.name
+            if "csm::" in name:
+                key = name.split("<")[0].split("(")[0].replace("void ", "")
+            elif name.startswith("_ZN3csm"):   # a mangled kernel name
+                key = "csm::" + name[7:].lstrip("0123456789").split("I")[0]
+            else:
+                if len(seen) < 8 and name not in seen:
+                    seen.append(name)
+                continue
+            names[key] = names.get(key, 0) + 1
+        if not names:
+            return None, "no kernel of the library among the profiled events: %s" % ", ".join(seen)
+        return sum(names.values()), names
     except Exception as e:  # profiler missing on this build: no claim
         return None, "not counted: %s" % type(e).__name__
 

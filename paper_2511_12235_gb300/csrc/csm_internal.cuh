@@ -235,6 +235,12 @@ struct LineF {
         ya = local(p, c);
         yb = local(p + d, c);
     }
+    // offsets at the walk faces w, w + 1, w + 2 (two neighbouring columns)
+    __device__ __forceinline__ void offsets3(int c, float& ya, float& yb, float& yc) const {
+        ya = local(p, c);
+        yb = local(p + d, c);
+        yc = local(p + 2 * d, c);
+    }
 };
 
 struct LineD {
@@ -250,6 +256,11 @@ struct LineD {
     __device__ __forceinline__ void offsets(int c, double& ya, double& yb) const {
         ya = p - (double)c;
         yb = (p + d) - (double)c;
+    }
+    __device__ __forceinline__ void offsets3(int c, double& ya, double& yb, double& yc) const {
+        ya = p - (double)c;
+        yb = (p + d) - (double)c;
+        yc = (p + 2.0 * d) - (double)c;
     }
 };
 

@@ -131,9 +131,22 @@ template <int NB> struct Cell<float, NB> {
             for (int r = 0; r < NB; ++r) (&v[0].x)[r] = __ldg(base + r);
         }
     }
+    // pairs of items with the packed FP32x2 FMA (one instruction per two items, the same
+    // IEEE fused multiply-add per item as the scalar form)
     __device__ __forceinline__ void fma(float (&acc)[NB], float wt) const {
+        if constexpr (NB % 2 == 0) {
+            const float2 w2 = make_float2(wt, wt);
 #pragma unroll
-        for (int i = 0; i < NB; ++i) acc[i] += wt * (&v[0].x)[i];
+            for (int i = 0; i < NB; i += 2) {
+                const float2 a = __ffma2_rn(make_float2((&v[0].x)[i], (&v[0].x)[i + 1]), w2,
+                                            make_float2(acc[i], acc[i + 1]));
+                acc[i] = a.x;
+                acc[i + 1] = a.y;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) acc[i] += wt * (&v[0].x)[i];
+        }
     }
 };
 template <int NB> struct Cell<double, NB> {
@@ -295,69 +308,122 @@ __device__ __forceinline__ bool pixel_elements(const Geo& g, int v, T X0, T X1, 
 }
 
 // ---------------------------------------------------------------------------------------
-// Back projection, gather form: each pixel's views are split over BG thread groups of one
-// block (views v = g, g + BG, ...); each thread loops over its views and the elements of its
-// footprint accumulating  W * p  in registers, then the groups' partial sums are added in
-// shared memory in a fixed order (deterministic, no atomics).  The same cell atoms as the
-// forward kernel give the same entries up to the FP32 rounding of the offsets.
+// Back projection, gather form, two pixels per thread.  A block holds a 16 x 8 pixel tile and
+// BG view groups (views v = g, g + BG, ...).  Each thread takes two pixels that are
+// neighbours along the view's walk axis: for the views walked along x (axis 0) the pairs
+// (ix, ix + 1), for the views walked along y the pairs (iy, iy + 1), so every thread runs two
+// phases with two different pairs.  The two pixels of a pair lie in neighbouring columns of
+// the same cell row, so they share
+//   - the element range (the projection of the 2 x 1 rectangle's four corners),
+//   - the corner lines: one line load gives the offsets at the walk faces w, w + 1, w + 2,
+//   - each element's NB sinogram values (one load serves both pixels' entries),
+// while each keeps its own cell atoms and sums.  An element outside one pixel's footprint
+// gets an exact zero weight there (both corner lines' atoms are 0 or both are 1).  The
+// phases' and groups' sums meet in shared memory and are added in a fixed order
+// (deterministic, no atomics).  The same cell atoms as the forward kernel give the same
+// entries up to the FP32 rounding of the offsets.
 // ---------------------------------------------------------------------------------------
-constexpr int BTX = 16, BTY = 4, BG = 4;   // pixel tile 16 x 4, 4 view groups: 256 threads
+constexpr int BTX = 16, BTY = 8, BG = 4;        // pixel tile 16 x 8, 4 view groups
+constexpr int kBackPix = BTX * BTY;              // pixels per tile
+constexpr int kBackThreads = kBackPix / 2 * BG;  // one pair per thread and group: 256
 
 template <typename T, int NB>
-__global__ void __launch_bounds__(BTX * BTY * BG) back2d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x,
-                                                           int xdt, int B, int b_off, T scale, int accumulate) {
+__device__ __forceinline__ void back_pair_phase(const Geo& g, const T* __restrict__ ps, int phase, int grp, int w,
+                                                int c, T RX0, T RX1, T RY0, T RY1, T (&acc1)[NB],
+                                                T (&acc2)[NB]) {
     constexpr int VW = Vec<NB>::W, Q = Vec<NB>::Q;
-    __shared__ T part[BG - 1][BTX * BTY][NB];
-    const int ix = blockIdx.x * BTX + threadIdx.x, iy = blockIdx.y * BTY + threadIdx.y;
-    const int grp = threadIdx.z;
-    const bool inside = ix < g.nx && iy < g.ny;
-    T acc[NB];
-#pragma unroll
-    for (int i = 0; i < NB; ++i) acc[i] = T(0);
-    if (inside) {
-        const T X0 = GeoT<T>::x0(g) + ix * GeoT<T>::a(g), X1 = X0 + GeoT<T>::a(g);
-        const T Y0 = GeoT<T>::y0(g) + iy * GeoT<T>::b(g), Y1 = Y0 + GeoT<T>::b(g);
-        using L = typename LineOf<T>::type;
-        const size_t plane = (size_t)g.nu * VW;
-        for (int v = grp; v < g.n_views; v += BG) {
-            int k0, k1;
-            if (!pixel_elements<T>(g, v, X0, X1, Y0, Y1, k0, k1)) continue;
-            const int axis = g.axis_sigma[2 * v], sigma = g.axis_sigma[2 * v + 1];
-            const int w = axis == 0 ? ix : iy, c = axis == 0 ? iy : ix;
-            L l;
-            l.load(g, v, k0, w);
-            T y0, y1;
-            l.offsets(c, y0, y1);
-            T prev = cell_atom(y0, y1, inv_of<T>(g, v, k0));
-            const T* pv = ps + (size_t)v * Q * plane;
-            for (int k = k0; k <= k1; ++k) {
-                Cell<T, NB> cell;
-                cell.load(pv + (size_t)k * VW, plane);   // issued before the weight arithmetic
-                l.load(g, v, k + 1, w);
-                l.offsets(c, y0, y1);
-                const T cur = cell_atom(y0, y1, inv_of<T>(g, v, k + 1));
-                const T wt = sigma > 0 ? cur - prev : prev - cur;
-                prev = cur;
-                cell.fma(acc, wt);
-            }
+    using L = typename LineOf<T>::type;
+    const size_t plane = (size_t)g.nu * VW;
+    for (int v = grp; v < g.n_views; v += BG) {
+        if (g.axis_sigma[2 * v] != phase) continue;
+        int k0, k1;
+        if (!pixel_elements<T>(g, v, RX0, RX1, RY0, RY1, k0, k1)) continue;
+        const int sigma = g.axis_sigma[2 * v + 1];
+        L l;
+        l.load(g, v, k0, w);
+        T y0, y1, y2;
+        l.offsets3(c, y0, y1, y2);
+        T inv = inv_of<T>(g, v, k0);
+        T prev1 = cell_atom(y0, y1, inv), prev2 = cell_atom(y1, y2, inv);
+        const T* pv = ps + (size_t)v * Q * plane;
+        for (int k = k0; k <= k1; ++k) {
+            Cell<T, NB> cell;
+            cell.load(pv + (size_t)k * VW, plane);   // issued before the weight arithmetic
+            l.load(g, v, k + 1, w);
+            l.offsets3(c, y0, y1, y2);
+            inv = inv_of<T>(g, v, k + 1);
+            const T cur1 = cell_atom(y0, y1, inv), cur2 = cell_atom(y1, y2, inv);
+            const T wt1 = sigma > 0 ? cur1 - prev1 : prev1 - cur1;
+            const T wt2 = sigma > 0 ? cur2 - prev2 : prev2 - cur2;
+            prev1 = cur1;
+            prev2 = cur2;
+            cell.fma(acc1, wt1);
+            cell.fma(acc2, wt2);
         }
     }
-    const int pix = threadIdx.y * BTX + threadIdx.x;
-    if (grp > 0) {
+}
+
+// shared memory: BG x NB x kBackPix sums (pixel innermost: conflict-free in both directions)
+template <typename T, int NB> constexpr size_t back2d_smem() { return (size_t)BG * NB * kBackPix * sizeof(T); }
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(kBackThreads) back2d_vox(Geo g, const T* __restrict__ ps, void* __restrict__ x,
+                                                         int xdt, int B, int b_off, T scale, int accumulate) {
+    extern __shared__ __align__(16) unsigned char back_smem[];
+    T* part = reinterpret_cast<T*>(back_smem);   // [BG][NB][kBackPix]
+    const int tid = threadIdx.x;
+    const int grp = tid / (kBackPix / 2), t = tid % (kBackPix / 2);
+    const int bx = blockIdx.x * BTX, by = blockIdx.y * BTY;
+    T* mine = part + (size_t)grp * NB * kBackPix;
+    const T A = GeoT<T>::a(g), Bh = GeoT<T>::b(g), XO = GeoT<T>::x0(g), YO = GeoT<T>::y0(g);
+    T acc1[NB], acc2[NB];
+
+    // phase 0: views walked along x, pairs (ix, ix + 1)
+    {
+        const int px = 2 * (t % (BTX / 2)), py = t / (BTX / 2);
+        const int ix = bx + px, iy = by + py;
 #pragma unroll
-        for (int i = 0; i < NB; ++i) part[grp - 1][pix][i] = acc[i];
-    }
-    __syncthreads();
-    if (grp == 0 && inside) {
-#pragma unroll
-        for (int gg = 0; gg < BG - 1; ++gg)
-#pragma unroll
-            for (int i = 0; i < NB; ++i) acc[i] += part[gg][pix][i];
+        for (int i = 0; i < NB; ++i) acc1[i] = acc2[i] = T(0);
+        if (ix < g.nx && iy < g.ny) {
+            const T X0 = XO + ix * A, Y0 = YO + iy * Bh;
+            back_pair_phase<T, NB>(g, ps, 0, grp, ix, iy, X0, X0 + 2 * A, Y0, Y0 + Bh, acc1, acc2);
+        }
+        const int p0 = py * BTX + px;
 #pragma unroll
         for (int i = 0; i < NB; ++i) {
-            const int b = b_off + i;
-            if (b < B) store_any<T>(x, ((size_t)b * g.ny + iy) * g.nx + ix, xdt, acc[i] * scale, accumulate != 0);
+            mine[i * kBackPix + p0] = acc1[i];
+            mine[i * kBackPix + p0 + 1] = acc2[i];
         }
+    }
+    // phase 1: views walked along y, pairs (iy, iy + 1)
+    const int qx = t % BTX, qy = 2 * (t / BTX);
+    {
+        const int ix = bx + qx, iy = by + qy;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) acc1[i] = acc2[i] = T(0);
+        if (ix < g.nx && iy < g.ny) {
+            const T X0 = XO + ix * A, Y0 = YO + iy * Bh;
+            back_pair_phase<T, NB>(g, ps, 1, grp, iy, ix, X0, X0 + A, Y0, Y0 + 2 * Bh, acc1, acc2);
+        }
+    }
+    __syncthreads();   // every phase-0 sum is in shared memory
+    {
+        const int p0 = qy * BTX + qx;
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            mine[i * kBackPix + p0] += acc1[i];
+            mine[i * kBackPix + p0 + BTX] += acc2[i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * kBackPix; e += kBackThreads) {
+        const int i = e / kBackPix, pix = e % kBackPix;
+        const int ix = bx + pix % BTX, iy = by + pix / BTX, b = b_off + i;
+        if (ix >= g.nx || iy >= g.ny || b >= B) continue;
+        T s = part[e];
+#pragma unroll
+        for (int gg = 1; gg < BG; ++gg) s += part[(size_t)gg * NB * kBackPix + e];
+        store_any<T>(x, ((size_t)b * g.ny + iy) * g.nx + ix, xdt, s * scale, accumulate != 0);
     }
 }
 
@@ -587,12 +653,17 @@ static csm_status run_back(const csm_geom_s* gh, const void* p, void* x, int64_t
     T* ps = (T*)ws;
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1) : T(gh->a * gh->b);
     const size_t n = (size_t)gh->n_views * gh->nu;
+    constexpr size_t smem = back2d_smem<T, NB>();
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(back2d_vox<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
+    }
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0,
                                                                          gh->n_views, gh->nu, ps);
-        dim3 bb(BTX, BTY, BG), bg((gh->nx + BTX - 1) / BTX, (gh->ny + BTY - 1) / BTY);
-        back2d_vox<T, NB><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
-                                            (flags & CSM_ACCUMULATE) ? 1 : 0);
+        dim3 bb(kBackThreads), bg((gh->nx + BTX - 1) / BTX, (gh->ny + BTY - 1) / BTY);
+        back2d_vox<T, NB><<<bg, bb, smem, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
+                                               (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
         if (e != CSM_OK) return e;
     }
