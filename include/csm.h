@@ -228,6 +228,13 @@ csm_status csm_dot_noalloc(const void* a, const void* c, int64_t n, int64_t batc
 csm_status csm_fma_rate(csm_dtype dt, int64_t iters, int blocks_per_sm, int launches,
                         double* flops, double* seconds, void* cuda_stream);
 
+/* The paper has no counterpart: instrumentation.  Writes to *count the number of kernels this
+ * library has launched from the host since it was loaded, on every device and stream (every
+ * launch site increments one process-wide counter just before it launches).  Replays of a
+ * CUDA graph that captured library launches are not counted again.  Differences of two
+ * readings count the launches of the calls in between.  Errors: CSM_EINVAL (count NULL). */
+csm_status csm_launch_count(uint64_t* count);
+
 /* ---- line-based comparator projectors ----------------------------------------------------
  * The line-integration system matrices the paper compares the consistent one with (Section
  * "Related work": Siddon's and Joseph's methods among the line-based approaches; Section

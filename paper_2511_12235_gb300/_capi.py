@@ -77,6 +77,8 @@ lib.csm_dot_noalloc.restype = _st
 lib.csm_fma_rate.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double),
                              C.c_void_p]
 lib.csm_fma_rate.restype = _st
+lib.csm_launch_count.argtypes = [C.POINTER(C.c_uint64)]
+lib.csm_launch_count.restype = _st
 lib.csm_forward_line.argtypes = [csm_geom_t, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int,
                                  C.c_int, C.c_void_p]
 lib.csm_forward_line.restype = _st
@@ -108,7 +110,8 @@ EXPORTED = [
     "csm_geom_create_2d", "csm_geom_create_3d", "csm_geom_free", "csm_workspace_bytes",
     "csm_forward", "csm_back", "csm_nnz", "csm_sync_status", "csm_status_string",
     "csm_last_cuda_error", "csm_dot_workspace_bytes", "csm_dot", "csm_axpby", "csm_dot_noalloc",
-    "csm_fma_rate", "csm_export_workspace_bytes", "csm_export_csr", "csm_csr_spmv", "csm_csr_normalize_rows",
+    "csm_fma_rate", "csm_launch_count", "csm_export_workspace_bytes", "csm_export_csr", "csm_csr_spmv",
+    "csm_csr_normalize_rows",
     "csm_ediv", "csm_fista_coeffs", "csm_forward_line", "csm_back_line", "csm_geom_set_element_weights",
 ]
 CSM_DOT_NOALLOC_MAX_BATCH = 64
@@ -193,6 +196,13 @@ def csm_fma_rate(dt, iters, blocks_per_sm, launches, stream) -> tuple[float, flo
     f, t = C.c_double(), C.c_double()
     check(lib.csm_fma_rate(dt, iters, blocks_per_sm, launches, C.byref(f), C.byref(t), stream), "csm_fma_rate")
     return f.value, t.value
+
+
+def csm_launch_count() -> int:
+    """Kernels the library has launched from the host so far (all devices and streams)."""
+    n = C.c_uint64()
+    check(lib.csm_launch_count(C.byref(n)), "csm_launch_count")
+    return n.value
 
 
 def csm_export_workspace_bytes(h, flags) -> int:

@@ -4,6 +4,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <new>
 
@@ -16,6 +17,9 @@ static thread_local char g_cuda_err[256] = {0};
 void set_cuda_error(cudaError_t e) {
     snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
 }
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 csm_status check_launch() {
     cudaError_t e = cudaGetLastError();
@@ -457,3 +461,9 @@ const char* csm_status_string(csm_status s) {
 const char* csm_last_cuda_error(void) { return g_cuda_err; }
 
 }  // extern "C"
+
+extern "C" csm_status csm_launch_count(uint64_t* count) {
+    if (!count) return CSM_EINVAL;
+    *count = (uint64_t)g_launches.load(std::memory_order_relaxed);
+    return CSM_OK;
+}

@@ -121,6 +121,9 @@ constexpr int kMaxG = 6;
 // thread-local record of the last CUDA error text
 void set_cuda_error(cudaError_t e);
 csm_status check_launch();
+// counts one kernel launch issued from the host (every launch site of the library calls it
+// just before its <<< >>>; csm_launch_count reads the total)
+void note_launch();
 
 // ---------------------------------------------------------------------------------------
 // Element conversions for storage types.

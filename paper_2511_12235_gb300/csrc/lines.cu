@@ -246,9 +246,9 @@ csm_status csm_forward_line(csm_geom_t g, int model, int lines, const void* x, v
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     dim3 blk(128), grd((g->nu + 127) / 128, g->nv, g->n_views);
     for (int64_t b = 0; b < batch; ++b) {
-        if (dbl) line_fwd<double><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, x, (int)xdt, p, (int)pdt,
+        if (dbl) note_launch(), line_fwd<double><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, x, (int)xdt, p, (int)pdt,
                                                                         (int)b, flags & CSM_ACCUMULATE);
-        else line_fwd<float><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, x, (int)xdt, p, (int)pdt,
+        else note_launch(), line_fwd<float><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, x, (int)xdt, p, (int)pdt,
                                                                       (int)b, flags & CSM_ACCUMULATE);
         s = check_launch();
         if (s != CSM_OK) return s;
@@ -272,9 +272,9 @@ csm_status csm_back_line(csm_geom_t g, int model, int lines, const void* p, void
     }
     dim3 blk(128), grd((g->nu + 127) / 128, g->nv, g->n_views);
     for (int64_t b = 0; b < batch; ++b) {
-        if (xdt == CSM_F64) line_back<double><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, p, (int)pdt,
+        if (xdt == CSM_F64) note_launch(), line_back<double><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, p, (int)pdt,
                                                                                    (double*)x, (int)b);
-        else line_back<float><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, p, (int)pdt, (float*)x, (int)b);
+        else note_launch(), line_back<float><<<grd, blk, 0, (cudaStream_t)stream>>>(geo, model, lines, p, (int)pdt, (float*)x, (int)b);
         s = check_launch();
         if (s != CSM_OK) return s;
     }

@@ -55,9 +55,9 @@ extern "C" csm_status csm_fma_rate(csm_dtype dt, int64_t iters, int blocks_per_s
     e = cudaEventRecord(e0, st);
     for (int l = 0; l < launches && e == cudaSuccess; ++l) {
         if (dt == CSM_F32)
-            fma_chains<float><<<grid, kPeakThreads, 0, st>>>(iters, 1.0000001f, -1e-7f);
+            note_launch(), fma_chains<float><<<grid, kPeakThreads, 0, st>>>(iters, 1.0000001f, -1e-7f);
         else
-            fma_chains<double><<<grid, kPeakThreads, 0, st>>>(iters, 1.0000000001, -1e-10);
+            note_launch(), fma_chains<double><<<grid, kPeakThreads, 0, st>>>(iters, 1.0000000001, -1e-10);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaEventRecord(e1, st);

@@ -515,8 +515,8 @@ static csm_status run_forward_vox(const csm_geom_s* gh, const void* x, void* p, 
     for (int64_t b = 0; b < batch; ++b) {
         cudaError_t e = cudaMemsetAsync(pacc, 0, n * sizeof(T), st);
         if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
-        fwd2d_vox<T><<<bg, bb, 0, st>>>(g, x, (int)xdt, (int)b, pacc);
-        finish_scatter_2d<T><<<1216, 256, 0, st>>>(g, pacc, p, (int)pdt, (int)b, scale, (flags & CSM_ACCUMULATE) ? 1 : 0);
+        note_launch(), fwd2d_vox<T><<<bg, bb, 0, st>>>(g, x, (int)xdt, (int)b, pacc);
+        note_launch(), finish_scatter_2d<T><<<1216, 256, 0, st>>>(g, pacc, p, (int)pdt, (int)b, scale, (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status s = check_launch();
         if (s != CSM_OK) return s;
     }
@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(256) export2d_kernel(Geo g, ExportArgs ea) {
 csm_status export_2d(const csm_geom_s* gh, const ExportArgs& a, cudaStream_t st) {
     const Geo g = make_geo(gh);
     dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16);
-    if (a.dbl) export2d_kernel<double><<<bg, bb, 0, st>>>(g, a);
-    else export2d_kernel<float><<<bg, bb, 0, st>>>(g, a);
+    if (a.dbl) note_launch(), export2d_kernel<double><<<bg, bb, 0, st>>>(g, a);
+    else note_launch(), export2d_kernel<float><<<bg, bb, 0, st>>>(g, a);
     return check_launch();
 }
 
@@ -630,15 +630,15 @@ static csm_status run_forward(const csm_geom_s* gh, const void* x, void* p, int6
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1) : T(gh->a * gh->b);
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 pb(32, 8), pg((gh->nx + 31) / 32, (gh->ny + 31) / 32);
-        prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
+        note_launch(), prep_image_2d<T, NB><<<pg, pb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, xs0, xs1);
         // pairs of elements per thread when that still leaves 64 Ki threads
         const bool pair = (size_t)(gh->nu / 2) * gh->n_views >= 65536;
         dim3 fb(64), fg(pair ? (gh->nu + 31) / 32 : (gh->nu + 15) / 16, (gh->n_views + 3) / 4);
         if (pair)
-            fwd2d_ray<T, NB, 2><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+            note_launch(), fwd2d_ray<T, NB, 2><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
                                                   (flags & CSM_ACCUMULATE) ? 1 : 0);
         else
-            fwd2d_ray<T, NB, 1><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+            note_launch(), fwd2d_ray<T, NB, 1><<<fg, fb, 0, st>>>(g, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
                                                   (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
         if (e != CSM_OK) return e;
@@ -659,10 +659,10 @@ static csm_status run_back(const csm_geom_s* gh, const void* p, void* x, int64_t
         if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     }
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
-        prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0,
+        note_launch(), prep_sino_2d<T, NB><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0,
                                                                          gh->n_views, gh->nu, ps);
         dim3 bb(kBackThreads), bg((gh->nx + BTX - 1) / BTX, (gh->ny + BTY - 1) / BTY);
-        back2d_vox<T, NB><<<bg, bb, smem, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
+        note_launch(), back2d_vox<T, NB><<<bg, bb, smem, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale,
                                                (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status e = check_launch();
         if (e != CSM_OK) return e;
@@ -722,7 +722,7 @@ csm_status nnz_2d(const csm_geom_s* gh, int64_t* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(gh->t.counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     dim3 bb(16, 16), bg((gh->nx + 15) / 16, (gh->ny + 15) / 16);
-    nnz2d_kernel<<<bg, bb, 0, st>>>(g, gh->t.counter);
+    note_launch(), nnz2d_kernel<<<bg, bb, 0, st>>>(g, gh->t.counter);
     csm_status s = check_launch();
     if (s != CSM_OK) return s;
     unsigned long long h = 0;

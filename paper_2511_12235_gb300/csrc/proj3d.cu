@@ -1374,12 +1374,12 @@ static csm_status run_fwd3_vox(const csm_geom_s* gh, const void* x, void* p, int
     constexpr int ZW = 64;
     for (int64_t b = 0; b < batch; ++b) {
         dim3 tb(32, 8), tg((gh->nx + 31) / 32, (gh->nz + 31) / 32, gh->ny);
-        prep_vol_3d<T, 1><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b, gh->nx, gh->ny, gh->nz, xs0, xs1);
+        note_launch(), prep_vol_3d<T, 1><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b, gh->nx, gh->ny, gh->nz, xs0, xs1);
         cudaError_t e = cudaMemsetAsync(pacc, 0, nsino * sizeof(T), st);
         if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
         dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZW - 1) / ZW);
-        fwd3d_vox<T, ZW><<<bg, bb, 0, st>>>(g, xs0, pacc);
-        finish_scatter_3d<T><<<1216, 256, 0, st>>>(g, pacc, p, (int)pdt, (int)b, scale, (flags & CSM_ACCUMULATE) ? 1 : 0);
+        note_launch(), fwd3d_vox<T, ZW><<<bg, bb, 0, st>>>(g, xs0, pacc);
+        note_launch(), finish_scatter_3d<T><<<1216, 256, 0, st>>>(g, pacc, p, (int)pdt, (int)b, scale, (flags & CSM_ACCUMULATE) ? 1 : 0);
         csm_status s = check_launch();
         if (s != CSM_OK) return s;
     }
@@ -1494,8 +1494,8 @@ csm_status export_3d(const csm_geom_s* gh, const ExportArgs& a, cudaStream_t st)
     const Geo g = make_geo(gh);
     const size_t ncol = (size_t)gh->nx * gh->ny;
     dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZWN - 1) / ZWN);
-    if (a.dbl) export3d_kernel<double><<<bg, bb, 0, st>>>(g, a);
-    else export3d_kernel<float><<<bg, bb, 0, st>>>(g, a);
+    if (a.dbl) note_launch(), export3d_kernel<double><<<bg, bb, 0, st>>>(g, a);
+    else note_launch(), export3d_kernel<float><<<bg, bb, 0, st>>>(g, a);
     return check_launch();
 }
 
@@ -1519,7 +1519,7 @@ static csm_status launch_fwd3(const Geo& g, const csm_geom_s* gh, const T* xs0, 
         if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     }
     dim3 fb(32 * FW), fg((gh->nu + FW * KW - 1) / (FW * KW), gh->n_views, (gh->nv + rw - 1) / rw);
-    fwd3d_grp<T, NB, KW><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+    note_launch(), fwd3d_grp<T, NB, KW><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
                                               (flags & CSM_ACCUMULATE) ? 1 : 0);
     return check_launch();
 }
@@ -1537,7 +1537,7 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     const bool wide = (size_t)((gh->nu + 7) / 8) * gh->n_views >= 16384;
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 tb(32, 8), tg((gh->nx + 31) / 32, (gh->nz + 31) / 32, gh->ny);
-        prep_vol_3d<T, NB><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, gh->nz, xs0, xs1);
+        note_launch(), prep_vol_3d<T, NB><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, gh->nz, xs0, xs1);
         csm_status e = wide ? launch_fwd3<T, NB, 8>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st)
                             : launch_fwd3<T, NB, 4>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st);
         if (e != CSM_OK) return e;
@@ -1579,7 +1579,7 @@ static csm_status launch_back3(const Geo& g, const csm_geom_s* gh, const T* ps, 
     const int vg = back_view_group(gh, sizeof(T), xdt, sizeof(T) == 8);
     for (int v0 = 0; v0 < gh->n_views; v0 += vg) {
         const int acc = (v0 > 0 || (flags & CSM_ACCUMULATE)) ? 1 : 0;
-        back3d_vox<T, NB, ZW><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale, acc, v0,
+        note_launch(), back3d_vox<T, NB, ZW><<<bg, bb, 0, st>>>(g, ps, x, (int)xdt, (int)batch, (int)b0, scale, acc, v0,
                                                 std::min(v0 + vg, gh->n_views));
         csm_status s = check_launch();
         if (s != CSM_OK) return s;
@@ -1597,7 +1597,7 @@ static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_
     constexpr int kTop = sizeof(T) == 8 ? 128 : 512 / NB;   // largest window instantiated
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 tb(32, 8), tg((gh->nu + 1 + 31) / 32, (gh->nv + 2 + 31) / 32, gh->n_views);
-        prep_diff_3d<T, NB><<<tg, tb, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0, gh->nu, gh->nv, ps);
+        note_launch(), prep_diff_3d<T, NB><<<tg, tb, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0, gh->nu, gh->nv, ps);
         csm_status r;
         if (zw >= kTop) r = launch_back3<T, NB, kTop>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
         else if (zw >= 256) r = launch_back3<T, NB, (kTop >= 256 ? 256 : 64)>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
@@ -1650,7 +1650,7 @@ csm_status nnz_3d(const csm_geom_s* gh, int64_t* out, cudaStream_t st) {
     if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     const size_t ncol = (size_t)gh->nx * gh->ny;
     dim3 bb(32 * BW), bg((unsigned)((ncol + BW - 1) / BW), (gh->nz + ZWN - 1) / ZWN);
-    nnz3d_kernel<<<bg, bb, 0, st>>>(g, gh->t.counter);
+    note_launch(), nnz3d_kernel<<<bg, bb, 0, st>>>(g, gh->t.counter);
     csm_status s = check_launch();
     if (s != CSM_OK) return s;
     unsigned long long h = 0;

@@ -57,12 +57,12 @@ static size_t scan_tmp_elems(size_t n) {
 
 static csm_status scan_exclusive(long long* d, size_t n, long long* tmp, cudaStream_t st) {
     const size_t nb = (n + kScanBlock - 1) / kScanBlock;
-    scan_block<<<(unsigned)nb, kScanThreads, 0, st>>>(d, n, tmp);
+    note_launch(), scan_block<<<(unsigned)nb, kScanThreads, 0, st>>>(d, n, tmp);
     csm_status s = check_launch();
     if (s != CSM_OK || nb <= 1) return s;
     s = scan_exclusive(tmp, nb, tmp + al32(nb), st);
     if (s != CSM_OK) return s;
-    scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, n, tmp);
+    note_launch(), scan_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(d, n, tmp);
     return check_launch();
 }
 
@@ -204,8 +204,8 @@ csm_status csm_export_csr(csm_geom_t g, int flags, csm_dtype val_dt, int64_t* ro
     if (s != CSM_OK) return s;
     if (!tr) {
         const unsigned blocks = (unsigned)((nr + 127) / 128);
-        if (dbl) sort_rows<double><<<blocks, 128, 0, st>>>(nr, (const long long*)row_ptr, col_idx, (double*)val);
-        else sort_rows<float><<<blocks, 128, 0, st>>>(nr, (const long long*)row_ptr, col_idx, (float*)val);
+        if (dbl) note_launch(), sort_rows<double><<<blocks, 128, 0, st>>>(nr, (const long long*)row_ptr, col_idx, (double*)val);
+        else note_launch(), sort_rows<float><<<blocks, 128, 0, st>>>(nr, (const long long*)row_ptr, col_idx, (float*)val);
         s = check_launch();
         if (s != CSM_OK) return s;
     }
@@ -224,10 +224,10 @@ csm_status csm_csr_spmv(int64_t n_rows, const int64_t* row_ptr, const int32_t* c
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     cudaStream_t st = (cudaStream_t)stream;
     if (dt == CSM_F64)
-        csr_spmv_kernel<double><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, col_idx,
+        note_launch(), csr_spmv_kernel<double><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, col_idx,
                                                          (const double*)val, alpha, (const double*)x, beta, (double*)y);
     else
-        csr_spmv_kernel<float><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, col_idx,
+        note_launch(), csr_spmv_kernel<float><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, col_idx,
                                                         (const float*)val, (float)alpha, (const float*)x, (float)beta,
                                                         (float*)y);
     return check_launch();
@@ -243,10 +243,10 @@ csm_status csm_csr_normalize_rows(int64_t n_rows, const int64_t* row_ptr, void* 
     const unsigned blocks = (unsigned)((threads + 255) / 256);
     cudaStream_t st = (cudaStream_t)stream;
     if (dt == CSM_F64)
-        csr_normalize_kernel<double><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, (double*)val,
+        note_launch(), csr_normalize_kernel<double><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, (double*)val,
                                                               (double*)row_sums);
     else
-        csr_normalize_kernel<float><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, (float*)val,
+        note_launch(), csr_normalize_kernel<float><<<blocks, 256, 0, st>>>((size_t)n_rows, (const long long*)row_ptr, (float*)val,
                                                              (float*)row_sums);
     return check_launch();
 }

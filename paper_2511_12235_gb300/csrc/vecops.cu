@@ -133,8 +133,8 @@ size_t dot_workspace_bytes(int64_t batch) { return (size_t)batch * kDotBlocks * 
 csm_status dot_launch(const void* a, const void* b, int64_t n, int64_t batch, csm_dtype dt, double* out,
                       double* part, cudaStream_t st) {
     dim3 g1(kDotBlocks, (unsigned)batch);
-    dot_partial<<<g1, kDotThreads, 0, st>>>(a, b, (int)dt, n, part);
-    dot_final<<<(unsigned)batch, kDotThreads, 0, st>>>(part, out);
+    note_launch(), dot_partial<<<g1, kDotThreads, 0, st>>>(a, b, (int)dt, n, part);
+    note_launch(), dot_final<<<(unsigned)batch, kDotThreads, 0, st>>>(part, out);
     return check_launch();
 }
 
@@ -243,7 +243,7 @@ csm_status csm_axpby(int64_t n, int64_t batch, csm_dtype dt, double a_c, const d
     int64_t blocks = (n + 255) / 256;
     if (blocks > 1216) blocks = 1216;   // 8 blocks of 256 per SM on 152 SMs, grid-stride beyond
     dim3 grid((unsigned)blocks, (unsigned)batch);
-    axpby_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, batch, (int)dt, a_c, a_num, a_den, x, b_c, b_num, b_den,
+    note_launch(), axpby_kernel<<<grid, 256, 0, (cudaStream_t)stream>>>(n, batch, (int)dt, a_c, a_num, a_den, x, b_c, b_num, b_den,
                                                         y, flags);
     return check_launch();
 }
@@ -253,7 +253,7 @@ csm_status csm_fista_coeffs(int64_t batch, const double* theta_table, int n_tabl
     if (batch < 0 || n_table < 0 || (batch > 0 && (!k || !one_plus_theta || !theta || (n_table > 0 && !theta_table))))
         return CSM_EINVAL;
     if (batch == 0) return CSM_OK;
-    fista_coeffs_kernel<<<(unsigned)((batch + 127) / 128), 128, 0, (cudaStream_t)stream>>>(batch, theta_table, n_table,
+    note_launch(), fista_coeffs_kernel<<<(unsigned)((batch + 127) / 128), 128, 0, (cudaStream_t)stream>>>(batch, theta_table, n_table,
                                                                                           k, one_plus_theta, theta);
     return check_launch();
 }
@@ -264,7 +264,7 @@ csm_status csm_ediv(int64_t n, csm_dtype dt, const void* num, const void* den, v
     if (n == 0) return CSM_OK;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 1216) blocks = 1216;
-    ediv_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, (int)dt, num, den, out);
+    note_launch(), ediv_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(n, (int)dt, num, den, out);
     return check_launch();
 }
 

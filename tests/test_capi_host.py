@@ -32,6 +32,13 @@ def test_library_exports_every_declared_symbol(capi):
     assert set(capi.EXPORTED) == set(syms)
 
 
+def test_launch_count_on_host(capi):
+    """The launch counter reads without a GPU and never goes down; a NULL pointer is refused."""
+    a = capi.csm_launch_count()
+    assert a >= 0 and capi.csm_launch_count() >= a
+    assert capi.lib.csm_launch_count(None) == capi.CSM_EINVAL
+
+
 def test_status_strings(capi):
     for s in range(7):
         assert capi.lib.csm_status_string(s)
