@@ -647,14 +647,13 @@ __device__ __forceinline__ T kink_tail(const AtomP<T>& P, T gw, T q, T iq, bool 
     return fabs(q) * (use_m ? mv : mv + (x * P.A - P.M1));
 }
 
-// The plane (if any) that meets the bottom face of voxel iz inside the cell, and its K for the
-// whole-cell atom (slot 0) and each crossing line's atom (slots 1 .. ng), written to kslot.
-// Returns the plane's index, or -1; ra receives the first plane whose height at the cell
-// centre is at or above the face (0 .. nv + 1), ha and qa its height above the face (units of
-// c) and q when ra <= nv.  Requires cv.fast.
+// The plane (if any) that meets the bottom face of voxel iz inside the cell: returns its index
+// rb (or -1) with its height hb above the face (units of c), q and 1/|q|; ra receives the first
+// plane whose height at the cell centre is at or above the face (0 .. nv + 1), ha and qa its
+// height above the face and q when ra <= nv.  Requires cv.fast.
 template <typename T>
-__device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
-                                         const AtomP<T>& full, T* kslot, int& ra, T& ha, T& qa) {
+__device__ __forceinline__ int face_plane(const Geo& g, int iz, const ColumnView<T>& cv, int& ra, T& ha, T& qa,
+                                          T& hb, T& qb, T& iqb) {
     // nearest planes: q t_c / c = iz - nz/2 at the face, planes q_r = (v0 + r dv) / sdd
     const T fz = T(iz) - T(0.5) * T(g.nz);
     const T qf = G3<T>::div(fz, cv.dh + cv.dl);
@@ -663,7 +662,9 @@ __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<
     // the two planes around the face (plane heights increase with r)
     const int r0 = rfl < T(-1) ? -1 : (rfl > T(g.nv) ? g.nv : (int)rfl);
     int rb = -1;
-    T hb = T(0), qb = T(0), iqb = T(0);
+    hb = T(0);
+    qb = T(0);
+    iqb = T(0);
     ra = r0 + 1;
     ha = T(0);
     qa = T(0);
@@ -678,6 +679,16 @@ __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<
             if (fabs(h) < fabs(q) * cv.margin_c) { rb = r; hb = h; qb = q; iqb = iq; }
         }
     }
+    return rb;
+}
+
+// face_plane, and the plane's K for the whole-cell atom (slot 0) and each crossing line's atom
+// (slots 1 .. ng), written to kslot.
+template <typename T>
+__device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
+                                         const AtomP<T>& full, T* kslot, int& ra, T& ha, T& qa) {
+    T hb, qb, iqb;
+    const int rb = face_plane<T>(g, iz, cv, ra, ha, qa, hb, qb, iqb);
     const int na = cv.ng + 1;
     const T gw = hb * G3<T>::c(g);
 #pragma unroll
@@ -687,6 +698,53 @@ __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<
             if (rb >= 0) kv = kink_tail<T>(j == 0 ? full : atoms[j - 1], gw, qb, iqb, hb < T(0));
             kslot[j] = kv;
         }
+    }
+    return rb;
+}
+
+// Where the columns of one (voxel column, view) sit in the differenced sinogram: the first
+// crossing line k1, the boundary column bcol of the whole-cell lines (valid when bok) and the
+// sign sb it carries after telescoping.
+struct BackCols {
+    int k1, bcol;
+    bool bok;
+    float sb;
+};
+template <typename T>
+__device__ __forceinline__ BackCols back_cols(const Geo& g, const ColumnView<T>& cv) {
+    BackCols bc;
+    bc.bcol = cv.sigma > 0 ? cv.k_first + cv.ng : cv.k_first;
+    bc.bok = bc.bcol >= 0 && bc.bcol < g.nu;
+    bc.sb = cv.sigma > 0 ? 1.0f : -1.0f;
+    bc.k1 = cv.k_first + 1;
+    return bc;
+}
+
+// The back projection's term of one face f (the bottom face of voxel iz): with the plane rb that
+// meets it inside the cell and the K of each atom, F_f = sum over atoms of K times the atom's
+// column of the differenced sinogram at plane rb.  It enters voxel iz with + and voxel iz - 1
+// with - (Phi = base + K_iz - K_{iz+1}), so each face's term is formed once, by the lane of
+// the voxel above it.  Returns rb; ra, ha, qa as face_plane.
+template <typename T, int NB>
+__device__ __forceinline__ int face_back(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
+                                         const AtomP<T>& full, const T* __restrict__ qv, const BackCols& bc, int& ra,
+                                         T& ha, T& qa, T (&ff)[NB]) {
+    T hb, qb, iqb;
+    const int rb = face_plane<T>(g, iz, cv, ra, ha, qa, hb, qb, iqb);
+#pragma unroll
+    for (int n = 0; n < NB; ++n) ff[n] = T(0);
+    if (rb >= 0) {
+        const int ns = g.nv + 2;
+        const T gw = hb * G3<T>::c(g);
+        const bool below = hb < T(0);
+#pragma unroll
+        for (int j = 0; j < kMaxG; ++j)
+            if (j < cv.ng)
+                fma_vec<T, NB>(ff, kink_tail<T>(atoms[j], gw, qb, iqb, below),
+                               qv + (((size_t)(bc.k1 + j) * ns + rb) * 4 + 0) * NB);
+        if (bc.bok)
+            fma_vec<T, NB>(ff, T(bc.sb) * kink_tail<T>(full, gw, qb, iqb, below),
+                           qv + (((size_t)bc.bcol * ns + rb) * 4 + 2) * NB);
     }
     return rb;
 }
@@ -703,20 +761,18 @@ __device__ __forceinline__ int face_kink(const Geo& g, int iz, const ColumnView<
 // differenced projections (prep_diff_3d).
 template <typename T, int NB>
 __device__ __forceinline__ void voxel_back_fast(const Geo& g, int iz, const ColumnView<T>& cv, const AtomP<T>* atoms,
-                                                const AtomP<T>& full, const T* __restrict__ qv, int ra, T ha, T qa,
-                                                int rtop, int rb, const T* kb, int rt, const T* kt, T (&sum)[NB]) {
+                                                const AtomP<T>& full, const T* __restrict__ qv, const BackCols& bc,
+                                                int ra, T ha, T qa, int rtop, const T (&corr)[NB], T (&sum)[NB]) {
     const int ng = cv.ng;
     const int ns = g.nv + 2;
     const T c = G3<T>::c(g);
-    // boundary column of the whole-cell lines and its sign after telescoping
-    const int bcol = cv.sigma > 0 ? cv.k_first + ng : cv.k_first;
-    const bool bok = bcol >= 0 && bcol < g.nu;
-    const T sb = cv.sigma > 0 ? T(1) : T(-1);
-    const int k1 = cv.k_first + 1;   // first crossing line
+    const int bcol = bc.bcol, k1 = bc.k1;
+    const bool bok = bc.bok;
+    const T sb = T(bc.sb);
     auto at = [&](int i, int r, int comp) { return qv + (((size_t)i * ns + r) * 4 + comp) * NB; };
     T acc[NB];
 #pragma unroll
-    for (int n = 0; n < NB; ++n) acc[n] = T(0);
+    for (int n = 0; n < NB; ++n) acc[n] = corr[n];   // the two faces' terms
     const int rlo = ra < 0 ? 0 : ra, rhi = rtop > g.nv + 1 ? g.nv + 1 : rtop;
 #pragma unroll 1
     T q = qa, hr = ha;                  // the first plane's height came with ra
@@ -738,19 +794,6 @@ __device__ __forceinline__ void voxel_back_fast(const Geo& g, int iz, const Colu
     for (int j = 0; j < kMaxG; ++j)
         if (j < ng) fma_vec<T, NB>(acc, c * atoms[j].A, at(k1 + j, rhi, 1));
     if (bok) fma_vec<T, NB>(acc, sb * c * full.A, at(bcol, rhi, 3));
-    // face corrections
-    if (rb >= 0) {
-#pragma unroll
-        for (int j = 0; j < kMaxG; ++j)
-            if (j < ng) fma_vec<T, NB>(acc, kb[j + 1], at(k1 + j, rb, 0));
-        if (bok) fma_vec<T, NB>(acc, sb * kb[0], at(bcol, rb, 2));
-    }
-    if (rt >= 0) {
-#pragma unroll
-        for (int j = 0; j < kMaxG; ++j)
-            if (j < ng) fma_vec<T, NB>(acc, -kt[j + 1], at(k1 + j, rt, 0));
-        if (bok) fma_vec<T, NB>(acc, -sb * kt[0], at(bcol, rt, 2));
-    }
     const T sg = cv.sigma > 0 ? T(1) : T(-1);
 #pragma unroll
     for (int n = 0; n < NB; ++n) sum[n] = sg * acc[n];
@@ -840,14 +883,12 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
                                                       int B, int b_off, T scale, int accumulate, int v_begin, int v_end) {
     __shared__ AtomP<T> atoms_s[BW][kMaxG + 1];
     __shared__ T acc_s[BW][NB * ZW];
-    __shared__ T ks_s[BW][32 * kKs];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int col = blockIdx.x * BW + wid;
     if (col >= g.nx * g.ny) return;                       // whole warp leaves together
     const int ix = col % g.nx, iy = col / g.nx;
     const int zb = blockIdx.y * ZW, ze = min(zb + ZW, g.nz);
     AtomP<T>* atoms = atoms_s[wid];
-    T* ks = ks_s[wid];
     T* acc = acc_s[wid];                                  // acc[b * ZW + (iz - zb)]
     for (int i = lane; i < NB * ZW; i += 32) acc[i] = T(0);
     for (int v = v_begin; v < v_end; ++v) {
@@ -866,24 +907,25 @@ __global__ void __launch_bounds__(32 * BW, sizeof(T) == 8 ? 3 : 8) back3d_vox(Ge
         sink.pv = ps + (size_t)v * (g.nu + 1) * (g.nv + 2) * 4 * NB;
         sink.nv = g.nv;
         if (cv.fast) {
-            // 31 voxels per pass; lane 31 finds the face above the last of them
+            const BackCols bc = back_cols<T>(g, cv);
+            // 31 voxels per pass; lane 31 forms the term of the face above the last of them
             for (int zc = z0; zc <= z1; zc += 31) {
                 const int iz = zc + lane;
                 int ra = 0;
-                T ha = T(0), qa = T(0);
-                const int rb = iz <= z1 + 1 ? face_kink<T>(g, iz, cv, atoms, atoms[kMaxG], ks + lane * kKs, ra, ha, qa)
-                                            : -1;
-                __syncwarp();
-                const int rt = __shfl_down_sync(0xffffffffu, rb, 1);
+                T ha = T(0), qa = T(0), ff[NB];
+#pragma unroll
+                for (int i = 0; i < NB; ++i) ff[i] = T(0);
+                if (iz <= z1 + 1) face_back<T, NB>(g, iz, cv, atoms, atoms[kMaxG], sink.pv, bc, ra, ha, qa, ff);
                 const int rtop = __shfl_down_sync(0xffffffffu, ra, 1);
+                T corr[NB];
+#pragma unroll
+                for (int i = 0; i < NB; ++i) corr[i] = ff[i] - __shfl_down_sync(0xffffffffu, ff[i], 1);
                 if (lane < 31 && iz <= z1) {
                     T vs[NB];
-                    voxel_back_fast<T, NB>(g, iz, cv, atoms, atoms[kMaxG], sink.pv, ra, ha, qa, rtop, rb, ks + lane * kKs, rt,
-                                           ks + (lane + 1) * kKs, vs);
+                    voxel_back_fast<T, NB>(g, iz, cv, atoms, atoms[kMaxG], sink.pv, bc, ra, ha, qa, rtop, corr, vs);
 #pragma unroll
                     for (int i = 0; i < NB; ++i) acc[i * ZW + iz - zb] += vs[i];
                 }
-                __syncwarp();
             }
         } else {
             for (int iz = z0 + lane; iz <= z1; iz += 32) {
