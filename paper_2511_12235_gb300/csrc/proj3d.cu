@@ -1038,7 +1038,8 @@ __device__ __forceinline__ void cell_forward_fast(const Geo& g, const ColumnView
             }
         }
         const int izn = __shfl_down_sync(0xffffffffu, izr, 1);
-        T tv[kMaxG + 1][NB];
+        // in place: cp becomes T' = C'(l + 1) - C'(l)
+        T (&tv)[kMaxG + 1][NB] = cp;
 #pragma unroll
         for (int j = 0; j <= kMaxG; ++j) {
             if (j < na) {
@@ -1099,7 +1100,7 @@ struct RowSink {
         }
     }
 };
-constexpr int FWD_SMEM = 24 * 1024;  // shared-memory budget of one block's row sums
+constexpr int FWD_SMEM = 32 * 1024;  // shared-memory budget of one block's row sums (256 rows at KW = 8)
 
 template <typename T, int NB, int KW>
 __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo g, int rw, const T* __restrict__ xs0,
