@@ -43,7 +43,8 @@ size_t workspace_3d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
     const size_t vol = al256((size_t)g->nx * g->ny * g->nz * nb * es);
     // back: the differenced sinogram, 4 values per (view, corner 0..nu, plane slot 0..nv+1)
     const size_t sino = al256((size_t)g->n_views * (g->nu + 1) * (g->nv + 2) * 4 * nb * es);
-    if (op == 0) return 2 * vol;   // the volume in both walk layouts
+    // the volume in both walk layouts and each column's range of nonzero voxels
+    if (op == 0) return 2 * vol + al256((size_t)g->nx * g->ny * sizeof(int2));
     if (op == 2) {                 // voxel-driven forward: one item's layouts and its sinogram sums
         const size_t vol1 = al256((size_t)g->nx * g->ny * g->nz * es);
         return 2 * vol1 + al256((size_t)g->n_views * g->nv * g->nu * es);
@@ -198,6 +199,34 @@ __global__ void __launch_bounds__(256) prep_vol_3d(const void* __restrict__ x, i
         }
         __syncthreads();
     }
+}
+
+// First and last voxel of each column (ix, iy) that holds a nonzero value of the chunk's items
+// (lo > hi when there is none), from the z-innermost copy: one warp per column, the lanes
+// reading 32 neighbouring voxels at a time.  The forward skips columns without one and limits
+// the planes of the others to their range.
+template <typename T, int NB>
+__global__ void __launch_bounds__(256) col_range_3d(const T* __restrict__ xs0, int ncol, int nz,
+                                                    int2* __restrict__ rng) {
+    const int lane = threadIdx.x & 31;
+    const int col = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (col >= ncol) return;                               // whole warp leaves together
+    const T* __restrict__ xc = xs0 + (size_t)col * nz * NB;
+    int lo = 0x7fffffff, hi = -1;
+    for (int zb = 0; zb < nz; zb += 32) {
+        const int iz = zb + lane;
+        bool nzv = false;
+        if (iz < nz) {
+#pragma unroll
+            for (int i = 0; i < NB; ++i) nzv |= xc[(size_t)iz * NB + i] != T(0);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, nzv);
+        if (m) {
+            if (lo == 0x7fffffff) lo = zb + __ffs(m) - 1;
+            hi = zb + 31 - __clz(m);
+        }
+    }
+    if (lane == 0) rng[col] = make_int2(lo, hi);
 }
 
 // The back projection reads, per view, corner / element column i = 0 .. nu and plane slot
@@ -1104,8 +1133,9 @@ constexpr int FWD_SMEM = 32 * 1024;  // shared-memory budget of one block's row 
 
 template <typename T, int NB, int KW>
 __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo g, int rw, const T* __restrict__ xs0,
-                                                     const T* __restrict__ xs1, void* __restrict__ p, int pdt,
-                                                     int B, int b_off, T scale, int accumulate) {
+                                                     const T* __restrict__ xs1, const int2* __restrict__ rng,
+                                                     void* __restrict__ p, int pdt, int B, int b_off, T scale,
+                                                     int accumulate) {
     __shared__ AtomP<T> atoms_s[FW][kMaxG + 1];
     extern __shared__ __align__(16) unsigned char fwd_dyn[];   // [FW][KW][rw][NB] sums
     using L = typename LineOf<T>::type;
@@ -1151,6 +1181,8 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
         chi = min(chi, nc - 1);
         for (int cc = clo; cc <= chi; ++cc) {
             const int ix = axis == 0 ? w : cc, iy = axis == 0 ? cc : w;
+            const int2 cr = rng[(size_t)ix * g.ny + iy];   // the column's nonzero voxels
+            if (cr.x > cr.y) continue;                     // none: the cell adds nothing
             ColumnView<T> cv;
             column_view<T>(g, v, ix, iy, lane, cv, kg, kg + nk);
             if (!cv.ok) continue;                          // warp-uniform
@@ -1162,23 +1194,10 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
             const T* xcol = xs + ((size_t)w * nc + cc) * g.nz * NB;
-            // the voxels in reach that are nonzero: cells with none add nothing and are skipped
-            // before any table is built; planes below or above all of them add nothing either
-            int znz_lo = 0x7fffffff, znz_hi = -1;
-            for (int zb = izlo; zb <= izhi; zb += 32) {
-                const int iz = zb + lane;
-                bool nzv = false;
-                if (iz <= izhi) {
-#pragma unroll
-                    for (int i = 0; i < NB; ++i) nzv |= __ldg(xcol + (size_t)iz * NB + i) != T(0);
-                }
-                const unsigned mz = __ballot_sync(0xffffffffu, nzv);
-                if (mz) {
-                    if (znz_lo == 0x7fffffff) znz_lo = zb + __ffs(mz) - 1;
-                    znz_hi = zb + 31 - __clz(mz);
-                }
-            }
-            if (znz_hi < 0) continue;
+            // the nonzero voxels in reach: cells with none add nothing and are skipped before any
+            // table is built; planes below or above all of them add nothing either
+            const int znz_lo = max(cr.x, izlo), znz_hi = min(cr.y, izhi);
+            if (znz_lo > znz_hi) continue;
             __syncwarp();
             for (int it = lane; it < cv.ng * 5; it += 32) {
                 const int i = it / 5;
@@ -1553,7 +1572,7 @@ static int rows_per_warp(const csm_geom_s* g, int kw, int nb, size_t elem) {
 }
 
 template <typename T, int NB, int KW>
-static csm_status launch_fwd3(const Geo& g, const csm_geom_s* gh, const T* xs0, const T* xs1, void* p,
+static csm_status launch_fwd3(const Geo& g, const csm_geom_s* gh, const T* xs0, const T* xs1, const int2* rng, void* p,
                               int64_t batch, csm_dtype pdt, int64_t b0, T scale, int flags, cudaStream_t st) {
     const int rw = rows_per_warp(gh, KW, NB, sizeof(T));
     const size_t dyn = (size_t)FW * KW * rw * NB * sizeof(T);
@@ -1562,7 +1581,7 @@ static csm_status launch_fwd3(const Geo& g, const csm_geom_s* gh, const T* xs0, 
         if (e != cudaSuccess) { set_cuda_error(e); return CSM_ECUDA; }
     }
     dim3 fb(32 * FW), fg((gh->nu + FW * KW - 1) / (FW * KW), gh->n_views, (gh->nv + rw - 1) / rw);
-    note_launch(), fwd3d_grp<T, NB, KW><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, p, (int)pdt, (int)batch, (int)b0, scale,
+    note_launch(), fwd3d_grp<T, NB, KW><<<fg, fb, dyn, st>>>(g, rw, xs0, xs1, rng, p, (int)pdt, (int)batch, (int)b0, scale,
                                               (flags & CSM_ACCUMULATE) ? 1 : 0);
     return check_launch();
 }
@@ -1577,12 +1596,15 @@ static csm_status run_fwd3(const csm_geom_s* gh, const void* x, void* p, int64_t
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
     T* xs0 = (T*)ws;
     T* xs1 = (T*)((char*)ws + half);
+    int2* rng = (int2*)((char*)ws + 2 * half);
+    const int ncol = gh->nx * gh->ny;
     const bool wide = (size_t)((gh->nu + 7) / 8) * gh->n_views >= 16384;
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 tb(32, 8), tg((gh->nx + 31) / 32, (gh->nz + 31) / 32, gh->ny);
         note_launch(), prep_vol_3d<T, NB><<<tg, tb, 0, st>>>(x, (int)xdt, (int)batch, (int)b0, gh->nx, gh->ny, gh->nz, xs0, xs1);
-        csm_status e = wide ? launch_fwd3<T, NB, 8>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st)
-                            : launch_fwd3<T, NB, 4>(g, gh, xs0, xs1, p, batch, pdt, b0, scale, flags, st);
+        note_launch(), col_range_3d<T, NB><<<(unsigned)((ncol + 7) / 8), 256, 0, st>>>(xs0, ncol, gh->nz, rng);
+        csm_status e = wide ? launch_fwd3<T, NB, 8>(g, gh, xs0, xs1, rng, p, batch, pdt, b0, scale, flags, st)
+                            : launch_fwd3<T, NB, 4>(g, gh, xs0, xs1, rng, p, batch, pdt, b0, scale, flags, st);
         if (e != CSM_OK) return e;
     }
     return CSM_OK;

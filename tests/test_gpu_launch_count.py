@@ -1,7 +1,8 @@
 """The library's own launch counter (csm_launch_count) against the launches each projector
 call is known to make: 2D forward / back one layout kernel and one projector kernel per chunk
-of 16 batch items; 3D forward the volume layout kernel and one projector kernel; 3D back the
-differenced-sinogram kernel and one projector launch per group of views."""
+of 16 batch items; 3D forward the volume layout kernel, the columns' nonzero ranges and one
+projector kernel; 3D back the differenced-sinogram kernel and one projector launch per group
+of views."""
 import numpy as np
 import pytest
 
@@ -40,7 +41,7 @@ def test_launches_per_call_3d():
     x = torch.from_numpy(synth.ellipsoid_phantom(g["nx"], 0)).float().cuda()[None]
     p = P.forward(x)
     xb = P.back(p)
-    assert _count(lambda: P.forward(x, out=p)) == 2
+    assert _count(lambda: P.forward(x, out=p)) == 3   # layouts, nonzero ranges, projector
     # views in groups whose slices of the differenced sinogram (FP32, batch 1) fit in 64 MiB
     slice_bytes = (g["nu"] + 1) * (g["nv"] + 2) * 4 * 4
     group = max(1, min(g["n_views"], (64 << 20) // slice_bytes))
