@@ -1183,21 +1183,22 @@ __global__ void __launch_bounds__(32 * FW, sizeof(T) == 8 ? 3 : 6) fwd3d_grp(Geo
             const int ix = axis == 0 ? w : cc, iy = axis == 0 ? cc : w;
             const int2 cr = rng[(size_t)ix * g.ny + iy];   // the column's nonzero voxels
             if (cr.x > cr.y) continue;                     // none: the cell adds nothing
-            ColumnView<T> cv;
-            column_view<T>(g, v, ix, iy, lane, cv, kg, kg + nk);
-            if (!cv.ok) continue;                          // warp-uniform
-            // voxels of the column that the window's rows reach
-            T qq, iqq;
-            const T zlo = floor(plane_height(g, L0, 0, cv.dh, cv.dl, qq, iqq) - mz);
-            const T zhi = floor(plane_height(g, L0 + nrow, 0, cv.dh, cv.dl, qq, iqq) + mz);
+            // voxels of the column that the window's rows reach (from the column's centre depth)
+            T dh, dl, qq, iqq;
+            column_depth(g, v, ix, iy, dh, dl);
+            const T zlo = floor(plane_height(g, L0, 0, dh, dl, qq, iqq) - mz);
+            const T zhi = floor(plane_height(g, L0 + nrow, 0, dh, dl, qq, iqq) + mz);
             if (zhi < T(0) || zlo > T(g.nz - 1)) continue;
             const int izlo = zlo < T(0) ? 0 : (int)zlo;
             const int izhi = zhi > T(g.nz - 1) ? g.nz - 1 : (int)zhi;
-            const T* xcol = xs + ((size_t)w * nc + cc) * g.nz * NB;
             // the nonzero voxels in reach: cells with none add nothing and are skipped before any
-            // table is built; planes below or above all of them add nothing either
+            // set-up; planes below or above all of them add nothing either
             const int znz_lo = max(cr.x, izlo), znz_hi = min(cr.y, izhi);
             if (znz_lo > znz_hi) continue;
+            ColumnView<T> cv;
+            column_view<T>(g, v, ix, iy, lane, cv, kg, kg + nk);
+            if (!cv.ok) continue;                          // warp-uniform
+            const T* xcol = xs + ((size_t)w * nc + cc) * g.nz * NB;
             __syncwarp();
             for (int it = lane; it < cv.ng * 5; it += 32) {
                 const int i = it / 5;
