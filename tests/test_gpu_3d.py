@@ -85,7 +85,7 @@ def test_small_fp32_and_batch(csm):
 
 def test_row_windows_batch4(csm):
     """A tall detector (200 rows) and a batch of 4: the forward splits the rows into windows
-    (96 rows per warp at four batch items); every window and batch item against the oracle."""
+    (128 rows per warp at four batch items); every window and batch item against the oracle."""
     ang = synth.uniform_angles(6)
     g = synth.geometry(8, 8, 40, n_views=6, angles=ang, nu=24, nv=200, s=60.0, sdd=100.0, du=1.0, dv=0.6)
     g["dim"] = 3
@@ -96,11 +96,38 @@ def test_row_windows_batch4(csm):
     for i in range(4):
         ref = oracle.forward_3d(g, xs[i])
         assert per_view_rel(p[i], ref) < FP32_TOL
-        assert np.count_nonzero(ref[:, 96:, :]) > 0          # rows beyond the first window carry weight
+        assert np.count_nonzero(ref[:, 128:, :]) > 0         # rows beyond the first window carry weight
     ys = rng.uniform(size=(4,) + p.shape[1:])
     b = P.back(torch.from_numpy(ys).float().cuda()).cpu().numpy()
     for i in range(4):
         assert rel(b[i], oracle.back_3d(g, ys[i])) < FP32_TOL
+
+
+def test_sparse_columns_fp64(csm):
+    """The forward skips the columns without a nonzero voxel and limits the planes of the
+    others to their range of nonzero voxels: one nonzero voxel, a zero volume, two nonzero
+    voxels at the ends of one column (zeros between them), and a batch whose items are nonzero
+    in different columns, in FP64 against the oracle (a zero volume projects to exact zeros)."""
+    g = small_geom(9, 8, 6, 17, 11)
+    P = csm.Projector(g)
+    one = np.zeros((6, 8, 9))
+    one[3, 4, 5] = 1.0
+    ends = np.zeros((6, 8, 9))
+    ends[0, 2, 2], ends[5, 2, 2] = 0.7, 1.3
+    for x in (one, ends):
+        ref = oracle.forward_3d(g, x)
+        p = P.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert np.count_nonzero(ref) > 0
+        assert np.max(np.abs(p - ref)) <= 1e-11 * np.max(np.abs(ref))
+    p0 = P.forward(torch.zeros((6, 8, 9), dtype=torch.float64, device="cuda")).cpu().numpy()
+    assert not np.any(p0)
+    xs = np.zeros((2, 6, 8, 9))
+    xs[0, 1, 3, 4] = 1.0
+    xs[1, 4, 6, 7] = 2.0
+    p = P.forward(torch.from_numpy(xs).cuda()).cpu().numpy()
+    for i in range(2):
+        ref = oracle.forward_3d(g, xs[i])
+        assert np.max(np.abs(p[i] - ref)) <= 1e-11 * np.max(np.abs(ref))
 
 
 def test_adjoint_3d(csm):
