@@ -44,6 +44,11 @@ WORKLOADS = {
 #   back    93 flops per (voxel, view) = 75 + 18 per item, 7.85 entries per (voxel, view)
 #   forward 59 flops per plane row = 33 + 26 per item, 0.10 plane rows per entry on the phantom
 #           (rows outside the column's nonzero voxels are skipped), plus 1390 per cell set-up
+# The same rate counted per entry of the direct closed form (every entry's Phi differences
+# formed and applied one by one, as the paper's per-voxel procedure does): 2D two cell atoms
+# and their difference (12 flops); 3D one Phi (two relu integrals over a top-view atom, shared
+# by four entries) and the double difference (40 flops); one multiply-add per batch item.
+DIRECT_FLOPS = {2: (12.0, 2.0), 3: (40.0, 2.0)}
 ALG_FLOPS = {(2, "forward"): (12.0, 2.0), (2, "back"): (12.0, 2.0),
              (3, "back"): (9.6, 2.3), (3, "forward"): (4.35, 2.6)}
 L2_FLUSH_BYTES = 512 << 20
@@ -500,6 +505,8 @@ def run_ours(args, rank, world, local):
     # roofline of the dominant kernel (ALU bound: algorithmic flops / launch time)
     dom, t_dom = ("forward", t_fwd) if t_fwd >= t_back else ("back", t_back)
     fpe, fpb = ALG_FLOPS[(g["dim"], dom)]
+    dfe, dfb = DIRECT_FLOPS[g["dim"]]
+    direct = nnz * (dfe + dfb * batch) / (t_dom / 1e3) / 1e12
     flops = nnz * (fpe + fpb * batch)
     achieved = flops / (t_dom / 1e3) / 1e12
     fp64 = tdt == torch.float64
@@ -535,7 +542,11 @@ def run_ours(args, rank, world, local):
                                      "the back projection's launches over its view groups summed, like its time)",
                      "peak_note": "%s rate measured in this run by csm_fma_rate (of measured); algorithmic "
                                   "flops = nnz x (%.2f + %.2f x batch), the FP operations of the kernel as "
-                                  "implemented per entry" % (which, fpe, fpb)},
+                                  "implemented per entry" % (which, fpe, fpb),
+                     "direct_form": {"flops_per_entry": "%.0f + %.0f x batch" % DIRECT_FLOPS[g["dim"]],
+                                     "achieved": direct, "frac": direct / pk,
+                                     "note": "the same kernel time counted with the flops of the direct "
+                                             "per-entry closed form, which the fast forms replace"}},
         "alu_peak_measured": peak,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(x_pin.numel() * x_pin.element_size()),
