@@ -120,8 +120,12 @@ csm_status csm_geom_set_element_weights(csm_geom_t geom, const double* weights);
 
 /* Bytes of caller-provided device workspace that csm_forward / csm_back need for this
  * geometry, batch and arithmetic type (op: 0 = forward, 1 = back, 2 = forward with
- * CSM_VOXEL_DRIVEN).  The workspace holds the batch-interleaved copies of the input that the
- * kernels gather from (and the voxel-driven forward's sums). */
+ * CSM_VOXEL_DRIVEN, 3 = back into an x stored in another type than the arithmetic, e.g. BF16
+ * or F16: op 1's workspace and, in 3D, an FP32 / FP64 copy of a chunk of x in which the sums
+ * are formed before x is written, rounded once; csm_back accepts op 1's size too and then
+ * runs the 3D back projection in one launch over all views).  The workspace holds the
+ * batch-interleaved copies of the input that the kernels gather from (and the voxel-driven
+ * forward's sums). */
 csm_status csm_workspace_bytes(csm_geom_t geom, int op, int64_t batch, csm_dtype compute,
                                size_t* bytes);
 

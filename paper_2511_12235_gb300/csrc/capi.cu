@@ -396,7 +396,7 @@ csm_status csm_geom_set_element_weights(csm_geom_t g, const double* weights) {
 static bool valid_dtype(csm_dtype t) { return t == CSM_F32 || t == CSM_F64 || t == CSM_BF16 || t == CSM_F16; }
 
 csm_status csm_workspace_bytes(csm_geom_t g, int op, int64_t batch, csm_dtype compute, size_t* bytes) {
-    if (!g || !bytes || batch < 0 || op < 0 || op > 2 || !valid_dtype(compute)) return CSM_EINVAL;
+    if (!g || !bytes || batch < 0 || op < 0 || op > 3 || !valid_dtype(compute)) return CSM_EINVAL;
     bool dbl = compute == CSM_F64;
     *bytes = g->dim == 2 ? workspace_2d(g, op, batch, dbl) : workspace_3d(g, op, batch, dbl);
     return CSM_OK;

@@ -49,6 +49,7 @@ size_t workspace_3d(const csm_geom_s* g, int op, int64_t batch, bool dbl) {
         const size_t vol1 = al256((size_t)g->nx * g->ny * g->nz * es);
         return 2 * vol1 + al256((size_t)g->n_views * g->nv * g->nu * es);
     }
+    if (op == 3) return sino + vol;   // back into BF16 / F16 x: and the chunk's sums in FP32 (FP64)
     return sino;
 }
 
@@ -1628,7 +1629,8 @@ static int back_window(const csm_geom_s* g, bool dbl, int nb) {
 // slices of the differenced sinogram stay in L2 (about 64 MiB of them, one batch item's worth,
 // so that the grouping and the summation order do not depend on the batch) instead of every
 // warp reading its own view from DRAM.  Each group adds its sums to x (read-modify-write, one
-// warp per voxel, a fixed order); outputs in BF16 / F16 are written once, from all views.
+// warp per voxel, a fixed order).  Sums for x in another type (BF16, F16) go through an FP32
+// / FP64 copy when the workspace holds one (op 3), else one launch covers all views.
 static int back_view_group(const csm_geom_s* g, size_t elem, csm_dtype xdt, bool dbl) {
     const bool exact_x = dbl ? xdt == CSM_F64 : xdt == CSM_F32;
     const size_t slice = (size_t)(g->nu + 1) * (g->nv + 2) * 4 * elem;
@@ -1653,23 +1655,47 @@ static csm_status launch_back3(const Geo& g, const csm_geom_s* gh, const T* ps, 
     return CSM_OK;
 }
 
+// x (any storage type) from the FP32 / FP64 sums of a chunk of batch items, rounded once.
+template <typename T>
+__global__ void __launch_bounds__(256) sums_to_x_3d(const T* __restrict__ xacc, size_t n, void* __restrict__ x,
+                                                    int xdt, size_t off, int accumulate) {
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (size_t)gridDim.x * 256)
+        store_any3<T>(x, off + i, xdt, xacc[i], accumulate != 0);
+}
+
+// xacc: when not null, the chunk's sums are formed in this FP32 / FP64 copy (the view groups
+// adding into it) and then written to x in its storage type; else they go to x directly.
 template <typename T, int NB>
 static csm_status run_back3(const csm_geom_s* gh, const void* p, void* x, int64_t batch, csm_dtype pdt,
-                            csm_dtype xdt, int flags, void* ws, cudaStream_t st) {
+                            csm_dtype xdt, int flags, void* ws, T* xacc, cudaStream_t st) {
     const Geo g = make_geo(gh);
     T* ps = (T*)ws;
     const T scale = (flags & CSM_RELATIVE_WEIGHTS) ? T(1.0 / (gh->a * gh->b * gh->c)) : T(1);
     const int zw = back_window(gh, sizeof(T) == 8, NB);
     constexpr int kTop = sizeof(T) == 8 ? 128 : 512 / NB;   // largest window instantiated
+    const csm_dtype tdt = sizeof(T) == 8 ? CSM_F64 : CSM_F32;
+    const size_t nvox = (size_t)gh->nx * gh->ny * gh->nz;
     for (int64_t b0 = 0; b0 < batch; b0 += NB) {
         dim3 tb(32, 8), tg((gh->nu + 1 + 31) / 32, (gh->nv + 2 + 31) / 32, gh->n_views);
         note_launch(), prep_diff_3d<T, NB><<<tg, tb, 0, st>>>(g, p, (int)pdt, (int)batch, (int)b0, gh->nu, gh->nv, ps);
+        // target of the projector launches: x itself, or the chunk's sums (items 0 .. nbc - 1)
+        const int64_t nbc = std::min<int64_t>(NB, batch - b0);
+        void* xt = xacc ? (void*)xacc : x;
+        const csm_dtype xtdt = xacc ? tdt : xdt;
+        const int64_t bt = xacc ? nbc : batch, b0t = xacc ? 0 : b0;
+        const int ft = xacc ? (flags & ~CSM_ACCUMULATE) : flags;
         csm_status r;
-        if (zw >= kTop) r = launch_back3<T, NB, kTop>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
-        else if (zw >= 256) r = launch_back3<T, NB, (kTop >= 256 ? 256 : 64)>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
-        else if (zw == 128) r = launch_back3<T, NB, 128>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
-        else r = launch_back3<T, NB, 64>(g, gh, ps, x, batch, xdt, b0, scale, flags, st);
+        if (zw >= kTop) r = launch_back3<T, NB, kTop>(g, gh, ps, xt, bt, xtdt, b0t, scale, ft, st);
+        else if (zw >= 256) r = launch_back3<T, NB, (kTop >= 256 ? 256 : 64)>(g, gh, ps, xt, bt, xtdt, b0t, scale, ft, st);
+        else if (zw == 128) r = launch_back3<T, NB, 128>(g, gh, ps, xt, bt, xtdt, b0t, scale, ft, st);
+        else r = launch_back3<T, NB, 64>(g, gh, ps, xt, bt, xtdt, b0t, scale, ft, st);
         if (r != CSM_OK) return r;
+        if (xacc) {
+            note_launch(), sums_to_x_3d<T><<<1216, 256, 0, st>>>(xacc, (size_t)nbc * nvox, x, (int)xdt, (size_t)b0 * nvox,
+                                                                 (flags & CSM_ACCUMULATE) ? 1 : 0);
+            r = check_launch();
+            if (r != CSM_OK) return r;
+        }
     }
     return CSM_OK;
 }
@@ -1700,13 +1726,19 @@ csm_status back_3d(const csm_geom_s* g, const void* p, void* x, int64_t batch, c
     const bool dbl = xdt == CSM_F64 || pdt == CSM_F64;
     if (!ws || ws_bytes < workspace_3d(g, 1, batch, dbl)) return CSM_EINVAL;
     if ((g->nz + 63) / 64 > 65535 || g->n_views > 65535 || (g->nv + 31) / 32 > 65535) return CSM_EUNSUPPORTED;
+    // x in another type than the arithmetic (BF16, F16, FP32 under FP64): with the larger
+    // workspace (op 3) the sums are formed in an FP32 / FP64 copy, so that the back projection
+    // runs in view groups and x is still rounded once; else one launch over all views
+    const bool exact_x = dbl ? xdt == CSM_F64 : xdt == CSM_F32;
+    const size_t sino = workspace_3d(g, 1, batch, dbl);
+    void* xacc = (!exact_x && ws_bytes >= workspace_3d(g, 3, batch, dbl)) ? (char*)ws + sino : nullptr;
     switch (chunk3(batch)) {
-        case 4: return dbl ? run_back3<double, 4>(g, p, x, batch, pdt, xdt, flags, ws, st)
-                           : run_back3<float, 4>(g, p, x, batch, pdt, xdt, flags, ws, st);
-        case 2: return dbl ? run_back3<double, 2>(g, p, x, batch, pdt, xdt, flags, ws, st)
-                           : run_back3<float, 2>(g, p, x, batch, pdt, xdt, flags, ws, st);
-        default: return dbl ? run_back3<double, 1>(g, p, x, batch, pdt, xdt, flags, ws, st)
-                            : run_back3<float, 1>(g, p, x, batch, pdt, xdt, flags, ws, st);
+        case 4: return dbl ? run_back3<double, 4>(g, p, x, batch, pdt, xdt, flags, ws, (double*)xacc, st)
+                           : run_back3<float, 4>(g, p, x, batch, pdt, xdt, flags, ws, (float*)xacc, st);
+        case 2: return dbl ? run_back3<double, 2>(g, p, x, batch, pdt, xdt, flags, ws, (double*)xacc, st)
+                           : run_back3<float, 2>(g, p, x, batch, pdt, xdt, flags, ws, (float*)xacc, st);
+        default: return dbl ? run_back3<double, 1>(g, p, x, batch, pdt, xdt, flags, ws, (double*)xacc, st)
+                            : run_back3<float, 1>(g, p, x, batch, pdt, xdt, flags, ws, (float*)xacc, st);
     }
 }
 

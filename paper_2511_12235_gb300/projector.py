@@ -147,7 +147,8 @@ class Projector:
         else:
             out = out.view((B,) + tuple(self.vol_shape))
         compute = torch.float64 if torch.float64 in (pb.dtype, out.dtype) else torch.float32
-        ws = self.workspace(1, B, compute)
+        # x stored in another type: the workspace with room for the sums in the arithmetic type
+        ws = self.workspace(1 if out.dtype == compute else 3, B, compute)
         stream = torch.cuda.current_stream(self.device).cuda_stream
         with nvtx_range("csm_back"):
             capi.csm_back(self.handle, pb.data_ptr(), out.data_ptr(), B, _dt(pb.dtype), _dt(out.dtype), flags,

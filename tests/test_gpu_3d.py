@@ -266,6 +266,37 @@ def test_cone128_f16_storage(csm):
     assert_elementwise(got, want, bound, "f16 back")
 
 
+def test_back_half_storage_view_groups(csm):
+    """Back projection into BF16 / F16 x with the workspace that holds an FP32 copy of x (op 3):
+    the view groups add their sums into that copy in the same order as the FP32 path adds them
+    into an FP32 x, and x is rounded once, so the result is the FP32 result rounded to BF16 /
+    F16 bit for bit (also with CSM_ACCUMULATE).  With op 1's workspace the back projection
+    runs in one launch over all views: within one rounding step of the same values."""
+    from paper_2511_12235_gb300 import _capi as capi
+    g = synth.config("cone3d_128")
+    P = csm.Projector(g)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(11)
+    y = torch.rand((1,) + tuple(P.sino_shape), generator=gen, device="cuda")
+    b32 = P.back(y)
+    for dt in (torch.bfloat16, torch.float16):
+        bh = P.back(y, out_dtype=dt)
+        assert torch.equal(bh, b32.to(dt))
+        x0 = torch.rand(b32.shape, generator=gen, device="cuda").to(dt)
+        acc = P.back(y, out=x0.clone(), flags=capi.CSM_ACCUMULATE)
+        assert torch.equal(acc, (x0.float() + b32).to(dt))
+        ws1 = P.workspace(1, 1, torch.float32)
+        one = torch.empty(b32.shape, dtype=dt, device="cuda")
+        capi.csm_back(P.handle, y.data_ptr(), one.data_ptr(), 1, capi.CSM_F32,
+                      capi.CSM_BF16 if dt == torch.bfloat16 else capi.CSM_F16, 0, ws1.data_ptr(), ws1.numel(),
+                      torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        step = 2.0 ** -7 if dt == torch.bfloat16 else 2.0 ** -10       # one rounding step, relative
+        diff = (one.float() - bh.float()).abs()
+        assert bool((diff <= step * b32.abs() + 1e-30).all())
+    P.close()
+
+
 def test_batch_invariance_3d(csm):
     """A batch item's projections do not depend on its batch mates: the back projection is
     bit-identical for batch sizes 1, 2 and 3 (fixed summation order); the forward, which adds
