@@ -804,7 +804,6 @@ __device__ __forceinline__ void voxel_back_fast(const Geo& g, int iz, const Colu
 #pragma unroll
     for (int n = 0; n < NB; ++n) acc[n] = corr[n];   // the two faces' terms
     const int rlo = ra < 0 ? 0 : ra, rhi = rtop > g.nv + 1 ? g.nv + 1 : rtop;
-#pragma unroll 1
     T q = qa, hr = ha;                  // the first plane's height came with ra
     for (int r = rlo; r < rhi; ++r) {   // planes with their centre inside the voxel (r <= nv)
         T iq;
