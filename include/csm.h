@@ -147,7 +147,7 @@ csm_status csm_forward(csm_geom_t geom, const void* x, void* p, int64_t batch,
 
 /* x = W^T p, the adjoint of csm_forward with the same entries (Section "Algorithm 1" and
  * the paper's adjoint-mismatch check, Section "Numerical Experiments").  Gather form (one
- * thread per pixel in 2D, one lane per voxel in 3D, where the voxel's value is summed by
+ * thread per two neighbouring pixels in 2D, one lane per voxel in 3D, where the voxel's value is summed by
  * parts over a differenced sinogram), fixed summation order, no atomics.
  * Arguments as for csm_forward with the roles of x and p exchanged (workspace from
  * csm_workspace_bytes(op = 1)). */
