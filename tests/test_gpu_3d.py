@@ -297,6 +297,23 @@ def test_back_half_storage_view_groups(csm):
     P.close()
 
 
+def test_back_half_storage_batches(csm):
+    """The FP32 / FP64 copy of x with chunks of batch items: a batch of 3 (chunks of 2 and 1)
+    into BF16 x equals the FP32 batch rounded to BF16, and FP32 x under FP64 arithmetic (FP64
+    projections) equals the FP64 result rounded to FP32."""
+    g = small_geom(9, 8, 6, 17, 11)
+    P = csm.Projector(g)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12)
+    y = torch.rand((3,) + tuple(P.sino_shape), generator=gen, device="cuda")
+    b32 = P.back(y)
+    assert torch.equal(P.back(y, out_dtype=torch.bfloat16), b32.to(torch.bfloat16))
+    y64 = y.double()
+    b64 = P.back(y64)
+    assert torch.equal(P.back(y64, out_dtype=torch.float32), b64.float())
+    P.close()
+
+
 def test_batch_invariance_3d(csm):
     """A batch item's projections do not depend on its batch mates: the back projection is
     bit-identical for batch sizes 1, 2 and 3 (fixed summation order); the forward, which adds
