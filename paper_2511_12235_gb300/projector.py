@@ -86,7 +86,8 @@ class Projector:
 
     def workspace(self, op: int, batch: int, compute: torch.dtype) -> torch.Tensor:
         n = capi.csm_workspace_bytes(self.handle, op, batch, _dt(compute))
-        key = (op, compute)
+        # the back projection's two sizes (op 3 = op 1 and a copy of x) share one buffer
+        key = (1 if op == 3 else op, compute)
         buf = self._ws.get(key)
         if buf is None or buf.numel() < n:
             buf = torch.empty(max(n, 256), dtype=torch.uint8, device=self.device)
