@@ -285,15 +285,17 @@ def test_back_half_storage_view_groups(csm):
         x0 = torch.rand(b32.shape, generator=gen, device="cuda").to(dt)
         acc = P.back(y, out=x0.clone(), flags=capi.CSM_ACCUMULATE)
         assert torch.equal(acc, (x0.float() + b32).to(dt))
-        ws1 = P.workspace(1, 1, torch.float32)
+        n1 = capi.csm_workspace_bytes(P.handle, 1, 1, capi.CSM_F32)     # no room for the copy of x
+        ws1 = torch.empty(n1, dtype=torch.uint8, device="cuda")
         one = torch.empty(b32.shape, dtype=dt, device="cuda")
         capi.csm_back(P.handle, y.data_ptr(), one.data_ptr(), 1, capi.CSM_F32,
-                      capi.CSM_BF16 if dt == torch.bfloat16 else capi.CSM_F16, 0, ws1.data_ptr(), ws1.numel(),
+                      capi.CSM_BF16 if dt == torch.bfloat16 else capi.CSM_F16, 0, ws1.data_ptr(), n1,
                       torch.cuda.current_stream().cuda_stream)
         torch.cuda.synchronize()
         step = 2.0 ** -7 if dt == torch.bfloat16 else 2.0 ** -10       # one rounding step, relative
         diff = (one.float() - bh.float()).abs()
         assert bool((diff <= step * b32.abs() + 1e-30).all())
+        assert bool((diff > 0).any())       # the single launch sums in another order
     P.close()
 
 
