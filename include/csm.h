@@ -150,7 +150,8 @@ csm_status csm_forward(csm_geom_t geom, const void* x, void* p, int64_t batch,
  * thread per two neighbouring pixels in 2D, one lane per voxel in 3D, where the voxel's value is summed by
  * parts over a differenced sinogram), fixed summation order, no atomics.
  * Arguments as for csm_forward with the roles of x and p exchanged (workspace from
- * csm_workspace_bytes(op = 1)). */
+ * csm_workspace_bytes(op = 1); with x stored in another type than the arithmetic, op = 3
+ * gives the faster form in 3D, see there). */
 csm_status csm_back(csm_geom_t geom, const void* p, void* x, int64_t batch,
                     csm_dtype p_dt, csm_dtype x_dt, int flags,
                     void* workspace, size_t workspace_bytes, void* cuda_stream);
